@@ -1,0 +1,179 @@
+"""CPU oracle of the binary-fluid D3Q19 lattice Boltzmann timestep.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by the package smoke check
+and by the benchmark's CPU-baseline leg, never by the CUDA library or its
+Python binding.  It shares no code with the CUDA path.
+
+The arithmetic lives in ``lb_oracle.c`` (plain FP64 C, built with
+``-O2 -ffp-contract=off``); this module compiles it with gcc on first use
+and wraps it with ctypes over numpy arrays.  Three builds of the one source
+are made: ``serial`` (the oracle proper), ``omp`` (the same loops with
+OpenMP on, used only to time the baseline on all host cores) and
+``complex`` (``-DORC_COMPLEX``: every value is ``double complex``, for
+complex-step derivatives).
+
+Parameters are a dict with keys tau, tau_g, rho0, gamma, A, B, kappa.
+Fields are flat arrays in site order ``x + nx*(y + ny*z)``; distributions
+are ``[19][N]`` in the oracle's own velocity order (``velocity_set()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SRC = [os.path.join(_HERE, "lb_oracle.c")]
+_FLAGS = {
+    "serial": ["-O2", "-ffp-contract=off"],
+    "omp": ["-O2", "-ffp-contract=off", "-fopenmp"],
+    "complex": ["-O2", "-ffp-contract=off", "-DORC_COMPLEX"],
+}
+_LIBS: dict = {}
+_LOCK = threading.Lock()
+
+PARAM_ORDER = ("tau", "tau_g", "rho0", "gamma", "A", "B", "kappa")
+NV = 19
+
+
+def _so_path(kind: str) -> str:
+    return os.path.join(_BUILD, f"liblb_oracle_{kind}.so")
+
+
+def build(force: bool = False) -> None:
+    """Compile every oracle build with gcc (no-op when up to date)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    src_m = max(os.path.getmtime(s) for s in _SRC)
+    for kind, flags in _FLAGS.items():
+        so = _so_path(kind)
+        if not force and os.path.exists(so) and os.path.getmtime(so) >= src_m:
+            continue
+        tmp = so + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-std=c99", "-shared", "-fPIC", *flags, *_SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, so)
+
+
+def _lib(kind: str = "serial"):
+    with _LOCK:
+        if kind not in _LIBS:
+            build()
+            _LIBS[kind] = ctypes.CDLL(_so_path(kind))
+        return _LIBS[kind]
+
+
+def _dtype(kind):
+    return np.complex128 if kind == "complex" else np.float64
+
+
+def _arr(a, kind):
+    a = np.ascontiguousarray(a, dtype=_dtype(kind))
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _prm(params, kind):
+    return _arr(np.array([params[k] for k in PARAM_ORDER]), kind)
+
+
+def velocity_set():
+    """(c[19,3] int, w[19] float64) in the oracle's order."""
+    c = np.zeros(57, dtype=np.int32)
+    w = np.zeros(19)
+    _lib().orc_velocity_set(c.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p))
+    return c.reshape(19, 3), w
+
+
+def gradients(dims, phi, kind="serial"):
+    """(grad [3][N], lap [N]) of phi by the 7-point stencils."""
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    phi, pp = _arr(phi, kind)
+    grad = np.zeros(3 * n, dtype=_dtype(kind))
+    lap = np.zeros(n, dtype=_dtype(kind))
+    _lib(kind).orc_gradients(nx, ny, nz, pp, grad.ctypes.data_as(ctypes.c_void_p),
+                             lap.ctypes.data_as(ctypes.c_void_p))
+    return grad.reshape(3, n), lap
+
+
+def site_thermo(params, phi, d, lap, kind="serial"):
+    """(mu, P[3,3]) at one site."""
+    prm, pp = _prm(params, kind)
+    d, dp = _arr(d, kind)
+    mu = np.zeros(1, dtype=_dtype(kind))
+    P = np.zeros(9, dtype=_dtype(kind))
+    lib = _lib(kind)
+    if kind == "complex":
+        raise NotImplementedError("site_thermo is exposed for the FP64 build")
+    lib.orc_site_thermo(pp, ctypes.c_double(phi), dp, ctypes.c_double(lap),
+                        mu.ctypes.data_as(ctypes.c_void_p), P.ctypes.data_as(ctypes.c_void_p))
+    return float(mu[0]), P.reshape(3, 3)
+
+
+def site_equilibrium(params, rho, j, phi, d, lap):
+    """(feq[19], geq[19]) at one site (FP64 build)."""
+    prm, pp = _prm(params, "serial")
+    j, jp = _arr(j, "serial")
+    d, dp = _arr(d, "serial")
+    feq = np.zeros(19)
+    geq = np.zeros(19)
+    _lib().orc_site_equilibrium(pp, ctypes.c_double(rho), jp, ctypes.c_double(phi), dp,
+                                ctypes.c_double(lap), feq.ctypes.data_as(ctypes.c_void_p),
+                                geq.ctypes.data_as(ctypes.c_void_p))
+    return feq, geq
+
+
+def init(dims, params, phi0, u0=None, kind="serial"):
+    """Equilibrium initial state (f, g), each [19][N]."""
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    prm, pp = _prm(params, kind)
+    phi0, php = _arr(phi0, kind)
+    if u0 is not None:
+        u0, up = _arr(np.reshape(u0, (3 * n,)), kind)
+    else:
+        up = None
+    f = np.zeros(19 * n, dtype=_dtype(kind))
+    g = np.zeros(19 * n, dtype=_dtype(kind))
+    _lib(kind).orc_init(nx, ny, nz, pp, php, up, f.ctypes.data_as(ctypes.c_void_p),
+                        g.ctypes.data_as(ctypes.c_void_p))
+    return f.reshape(19, n), g.reshape(19, n)
+
+
+def step(dims, params, f, g, nsteps, kind="serial"):
+    """Advance (f, g) by ``nsteps``; returns new arrays (inputs untouched)."""
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    prm, pp = _prm(params, kind)
+    f = np.array(f, dtype=_dtype(kind), copy=True).reshape(-1)
+    g = np.array(g, dtype=_dtype(kind), copy=True).reshape(-1)
+    _lib(kind).orc_step(nx, ny, nz, pp, f.ctypes.data_as(ctypes.c_void_p),
+                        g.ctypes.data_as(ctypes.c_void_p), int(nsteps))
+    return f.reshape(19, n), g.reshape(19, n)
+
+
+def moments(dims, f, g, kind="serial"):
+    """(rho [N], u [3][N], phi [N])."""
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    f, fp = _arr(np.reshape(f, -1), kind)
+    g, gp = _arr(np.reshape(g, -1), kind)
+    rho = np.zeros(n, dtype=_dtype(kind))
+    u = np.zeros(3 * n, dtype=_dtype(kind))
+    phi = np.zeros(n, dtype=_dtype(kind))
+    _lib(kind).orc_moments(nx, ny, nz, fp, gp, rho.ctypes.data_as(ctypes.c_void_p),
+                           u.ctypes.data_as(ctypes.c_void_p), phi.ctypes.data_as(ctypes.c_void_p))
+    return rho, u.reshape(3, n), phi
+
+
+def reduce(dims, f, g, kind="serial"):
+    """[sum rho, sum rho u (3), sum phi]."""
+    nx, ny, nz = dims
+    f, fp = _arr(np.reshape(f, -1), kind)
+    g, gp = _arr(np.reshape(g, -1), kind)
+    out = np.zeros(5, dtype=_dtype(kind))
+    _lib(kind).orc_reduce(nx, ny, nz, fp, gp, out.ctypes.data_as(ctypes.c_void_p))
+    return out
