@@ -1,0 +1,340 @@
+"""Benchmark of the binary-fluid D3Q19 lattice Boltzmann step on GB300.
+
+A "step" is one timestep of the whole path (phi, 7-point stencil, fused f/g
+collision, pull streaming) over a 256^3 periodic lattice, FP32-shifted
+storage -- the fused-step-at-256^3 workload.  The same line also carries the
+FP64 form's MLUPS on the same lattice, the per-field error of both forms
+against the CPU oracle on a small sample, the roofline of the dominant
+kernel, an end-to-end number through the C ABI with host buffers, and the
+CPU oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the lattice
+(the step has no cross-lattice exchange): weak scaling, max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lb_inputs as LI  # noqa: E402
+
+DIMS = (256, 256, 256)
+BYTES_PER_SITE = {"fp32_shifted": 4 * 19 * 4, "fp64": 4 * 19 * 8}   # read+write f and g once
+METRIC = "MLUPS and % of HBM roofline (fused step), FP32-shifted vs FP64 at stated error"
+ORACLE_SAMPLE = (64, 64, 64)
+ORACLE_STEPS = 30
+E2E_STEPS = 50
+FALLBACK_HBM = 6800.0
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return FALLBACK_HBM, "fallback"
+
+
+def _kernel_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1405_6162_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(precision):
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", f"fused_step_{precision}_256cubed.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not (m_sha and m_b) or m_sha.group(1) != _kernel_sha():
+        return None
+    return float(m_b.group(1))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+        return False
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, fl in rows for k, v in enumerate(fl) if v.lower() == "active"})
+        sm = sorted(r[0] for r in rows)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _time_steps(lat, steps, torch):
+    """Per-launch CUDA-event times (s) of ``steps`` single-step launches."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for s, e in ev:
+        s.record()
+        lat.step(1)
+        e.record()
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) / 1e3 for s, e in ev]
+
+
+def _oracle_errors(torch, params):
+    """Per-field error of both GPU forms against the oracle on the sample,
+    plus the oracle's own timing (the CPU baseline)."""
+    import oracle
+    from paper_1405_6162_gb300 import Lattice
+    oracle.build()
+    dims = ORACLE_SAMPLE
+    phi0 = LI.spinodal_phi0(*dims, seed=1)
+    f, g = oracle.init(dims, params, phi0)
+    t0 = time.perf_counter()
+    f, g = oracle.step(dims, params, f, g, ORACLE_STEPS)
+    t_or = time.perf_counter() - t0
+    want = oracle.moments(dims, f, g)
+    errs = {}
+    for prec in ("fp64", "fp32_shifted"):
+        with Lattice.from_params(dims, params, precision=prec) as lat:
+            lat.init(phi0)
+            lat.step(ORACLE_STEPS)
+            got = lat.moments()
+        errs[prec] = {k: float(np.abs(a - b).max() / np.abs(b).max())
+                      for k, a, b in zip(("rho", "u", "phi"), got, want)}
+    n = int(np.prod(dims))
+    base = {"value": n * ORACLE_STEPS / t_or / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{dims[0]}^3 spinodal (seed 1) x {ORACLE_STEPS} steps, FP64 C oracle, 1 thread"}
+    return errs, base
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1405_6162_gb300 as lbpkg
+    from paper_1405_6162_gb300 import Lattice, tuning
+    lbpkg.build()
+    params = dict(LI.DEFAULT_PARAMS)
+    n = int(np.prod(DIMS))
+    phi0 = LI.spinodal_phi0(*DIMS, seed=1)
+    peak, peak_kind = _peaks()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if ws == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    for prec in ("fp32_shifted", "fp64"):
+        cfg = tuning.bench_config(DIMS, prec)
+        with Lattice.from_params(DIMS, params, precision=prec) as lat:
+            lat.set_kernel(*cfg)
+            lat.init(phi0)
+            lat.step(args.warmup)
+            barrier()
+            start = torch.cuda.Event(enable_timing=True)
+            stop = torch.cuda.Event(enable_timing=True)
+            with Clocks(local) as clk:
+                start.record()
+                lat.step(args.steps)
+                stop.record()
+                barrier()
+            wall = max_over_ranks(start.elapsed_time(stop) / 1e3)
+            # per-launch durations of the same kernel for the roofline
+            per = _time_steps(lat, max(5, min(args.steps, 20)), torch)
+            r = lat.reduce()
+        t_launch = float(np.mean(per))
+        results[prec] = dict(cfg=cfg, wall=wall, t_launch=t_launch, clocks=clk.summary(),
+                             mass=float(r[0]))
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    prec = "fp32_shifted"
+    phi_host = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+    phi_host[:] = phi0
+    out_host = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+    e2e_iters = 2
+    with Lattice.from_params(DIMS, params, precision=prec) as lat:
+        lat.set_kernel(*tuning.bench_config(DIMS, prec))
+        lat.init(phi_host)
+        lat.step(2)
+        lbl = lat.handle
+        lib = __import__("paper_1405_6162_gb300._lib", fromlist=["lib"]).lib()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_iters):
+            lat.init(phi_host)                       # H2D of the inputs
+            lat.step(E2E_STEPS)
+            rc = lib.lb_moments(lbl, None, None, out_host.ctypes.data, 0)   # D2H of the result
+            assert rc == 0
+        barrier()
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": ws * n * E2E_STEPS * e2e_iters / t_e2e / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": n * 8 / E2E_STEPS, "d2h_bytes_per_step": n * 8 / E2E_STEPS,
+           "steps_per_transfer": E2E_STEPS}
+
+    if rank != 0:
+        return
+    errs, cpu = (None, None)
+    if ws == 1:
+        errs, cpu = _oracle_errors(torch, params)
+
+    def line_for(prec):
+        r = results[prec]
+        mlups = ws * n * args.steps / r["wall"] / 1e6
+        achieved = BYTES_PER_SITE[prec] * n / r["t_launch"] / 1e9
+        traffic = _ncu_traffic(prec)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": BYTES_PER_SITE[prec] * n}
+        return mlups, roof
+
+    v32, roof32 = line_for("fp32_shifted")
+    v64, roof64 = line_for("fp64")
+    r32 = results["fp32_shifted"]
+    out = {
+        "metric": METRIC, "value": v32, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r32["wall"] / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "256^3 periodic D3Q19 binary fluid, spinodal phi0 ~ U[-0.01,0.01] seed 1, "
+                               "tau=1, tau_g=1, rho0=1, Gamma=0.5, A=-0.0625, B=0.0625, kappa=0.04; "
+                               "FP32-shifted fused step",
+                   "lattice": list(DIMS), "precision": "fp32_shifted",
+                   "launch": list(r32["cfg"]),
+                   "l2": "inputs larger than L2 (5.1 GB state vs 129 MB L2): no flush",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": roof32,
+        "fp64": {"value": v64, "unit": "MLUPS", "ms_per_step": results["fp64"]["wall"] / args.steps * 1e3,
+                 "roofline": roof64, "launch": list(results["fp64"]["cfg"]),
+                 "clocks": results["fp64"]["clocks"]},
+        "error_vs_oracle": ({"sample": f"{ORACLE_SAMPLE[0]}^3 spinodal seed 1, {ORACLE_STEPS} steps, "
+                                       "max|gpu-oracle| / max|oracle| per field", **errs} if errs else None),
+        "clocks": r32["clocks"],
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out))
+
+
+def run_reference(args):
+    """The CPU oracle timed as the reference arm, on a bounded sample."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    params = dict(LI.DEFAULT_PARAMS)
+    dims = ORACLE_SAMPLE
+    f, g = oracle.init(dims, params, LI.spinodal_phi0(*dims, seed=1))
+    for _ in range(args.warmup):
+        f, g = oracle.step(dims, params, f, g, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, g = oracle.step(dims, params, f, g, 1)
+    t = time.perf_counter() - t0
+    n = int(np.prod(dims))
+    v = n * args.steps / t / 1e6
+    sample = f"{dims[0]}^3 spinodal (seed 1), one oracle timestep per step, FP64 C oracle, 1 thread"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "256^3 periodic D3Q19 binary fluid (oracle timed on a 64^3 sample)",
+                   "lattice": list(dims), "precision": "fp64"},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

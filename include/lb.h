@@ -1,0 +1,184 @@
+/*
+ * lb.h -- C ABI of the GB300 (sm_103a) binary-fluid lattice Boltzmann library.
+ *
+ * One timestep of the symmetric binary fluid on a periodic D3Q19 lattice:
+ * phi = sum_i g_i, 7-point finite differences of phi, the fused BGK collision
+ * of the density distribution f (equilibrium carrying the free-energy
+ * pressure tensor) and of the order-parameter distribution g (equilibrium
+ * carrying Gamma*mu, mu = A phi + B phi^3 - kappa lap phi), then streaming.
+ * This is the "binary collision" benchmark of targetDP (Gray & Stratford,
+ * 2014), Sec. IV: an LB collision on a mixture of two fluids with inner
+ * extents 19 (momenta) and 3 (dimensions), on a lattice whose order parameter
+ * is advanced by finite differences (Sec. II.A).  The paper prints no
+ * equations; the model is written out beside lb_step below.
+ *
+ * The library surface restates the paper's host API (Sec. III.B memory
+ * management: targetMalloc / copyToTarget / copyFromTarget /
+ * copyConstant<X>ToTarget; Sec. III.C execution: TARGET_LAUNCH / syncTarget)
+ * as a stateful context: the library owns the device-side lattice (the
+ * paper's "target copy", Sec. III.A) and the caller owns every host or device
+ * array it passes in.
+ *
+ * Conventions (all entry points):
+ *  - Return LB_OK (0) on success or a negative LB_ERR_* code; nothing aborts.
+ *    lb_strerror() names a code, lb_last_error() gives the last CUDA error
+ *    text seen by the calling thread.
+ *  - Sites are ordered x fastest: s = x + nx*(y + ny*z), N = nx*ny*nz.
+ *    Scalar fields are double[N]; vector fields are SoA double[3][N];
+ *    distributions are SoA double[19][N] (value i of site s at i*N + s).
+ *  - Every array crossing the ABI is FP64 whatever the storage precision.
+ *  - ptr_kind says where a caller array lives: LB_HOST (pageable or pinned
+ *    host memory) or LB_DEVICE (device memory of the context's GPU).
+ *  - Work is ordered on the CUDA stream given at creation (NULL = the legacy
+ *    default stream).  Calls that return host data synchronise that stream;
+ *    calls on device pointers do not.
+ *  - A context must not be used from two threads at once.
+ *
+ * Velocity order of the distributions at the ABI (i: c_i, weight w_i):
+ *    0: ( 0, 0, 0) 1/3
+ *    1: (+1, 0, 0)  2: (-1, 0, 0)  3: ( 0,+1, 0)  4: ( 0,-1, 0)
+ *    5: ( 0, 0,+1)  6: ( 0, 0,-1)                               1/18
+ *    7: (+1,+1, 0)  8: (-1,-1, 0)  9: (+1,-1, 0) 10: (-1,+1, 0)
+ *   11: (+1, 0,+1) 12: (-1, 0,-1) 13: (+1, 0,-1) 14: (-1, 0,+1)
+ *   15: ( 0,+1,+1) 16: ( 0,-1,-1) 17: ( 0,+1,-1) 18: ( 0,-1,+1)  1/36
+ * Odd i and i+1 are opposite velocities.
+ */
+#ifndef LB_H
+#define LB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    LB_OK = 0,
+    LB_ERR_INVALID = -1,   /* bad argument, size or state                     */
+    LB_ERR_NOMEM = -2,     /* device allocation failed                        */
+    LB_ERR_CUDA = -3,      /* a CUDA call failed; see lb_last_error()         */
+    LB_ERR_NONFINITE = -4, /* a reduction found NaN or Inf in the state       */
+    LB_ERR_TIMEOUT = -5    /* a bounded device-side wait gave up              */
+};
+
+/* Storage/arithmetic precision of the distributions. */
+enum {
+    LB_FP64 = 0,          /* f, g stored and computed in double               */
+    LB_FP32_SHIFTED = 1   /* float storage and arithmetic of f_i - w_i rho0
+                             and of g_i; FP64 only in lb_reduce's sums         */
+};
+
+enum { LB_HOST = 0, LB_DEVICE = 1 };
+
+/* Step kernels selectable with lb_set_kernel(). */
+enum {
+    LB_KERNEL_AUTO = 0,     /* library default (the fused kernel)              */
+    LB_KERNEL_TWO_PASS = 1, /* phi pass + collide/stream pass (phi buffer)     */
+    LB_KERNEL_FUSED = 2     /* single pass, phi halo staged in shared memory   */
+};
+
+typedef struct lb_ctx lb_ctx;
+
+/* Physical and lattice parameters of one periodic lattice. */
+typedef struct {
+    int nx, ny, nz;   /* lattice extents, each >= 1                         */
+    double tau;       /* BGK relaxation time of f, > 1/2                    */
+    double tau_g;     /* relaxation time of g, > 1/2                        */
+    double rho0;      /* reference density (initial rho; the FP32 shift)    */
+    double gamma;     /* mobility parameter Gamma                           */
+    double A, B;      /* bulk free-energy coefficients                      */
+    double kappa;     /* interfacial (gradient) coefficient                 */
+    int precision;    /* LB_FP64 or LB_FP32_SHIFTED                         */
+} lb_params;
+
+/* Optional device allocator (e.g. a framework's caching allocator).
+ * alloc returns a device pointer of at least `bytes` (256-byte aligned) or
+ * NULL; free releases it.  `stream` is the context's stream. */
+typedef void *(*lb_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*lb_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+/* Install the allocator used by contexts created afterwards (process-wide;
+ * both NULL restores cudaMalloc/cudaFree).  A context keeps the allocator it
+ * was created with.  Returns LB_ERR_INVALID if exactly one of the two is NULL.
+ * Paper: targetMalloc / targetFree, Sec. III.B. */
+int lb_set_allocator(lb_alloc_fn alloc, lb_free_fn free_fn, void *user);
+
+/* Create a context: validates *p, allocates the two double-buffered SoA
+ * distribution arrays (2 x 2 x 19 x N values of 8 or 4 bytes) plus an N-site
+ * phi buffer and reduction scratch on the current CUDA device.  The state is
+ * undefined until lb_init or lb_set_state.  *out receives the context.
+ * Errors: LB_ERR_INVALID (NULL pointer, extent < 1, N >= 2^31, tau or tau_g
+ * <= 1/2, rho0 <= 0, unknown precision), LB_ERR_NOMEM, LB_ERR_CUDA.
+ * Paper: targetMalloc, Sec. III.B. */
+int lb_create(const lb_params *p, void *cuda_stream, lb_ctx **out);
+
+/* Release every device buffer of c (NULL is a no-op).  Synchronises c's
+ * stream first.  Paper: targetFree, Sec. III.B. */
+void lb_destroy(lb_ctx *c);
+
+/* Initial state: rho = rho0, u = u0 (u0 == NULL: fluid at rest), phi = phi0;
+ * the 7-point stencils of phi0 give mu and the pressure tensor, and f, g are
+ * set to their equilibria (computed in FP64, then stored in the context's
+ * precision).  phi0 is double[N], u0 SoA double[3][N], both in ptr_kind
+ * memory; they are read before the call returns (LB_HOST) or before later
+ * work on the stream (LB_DEVICE).  Errors: LB_ERR_INVALID, LB_ERR_CUDA.
+ * Paper: copyToTarget, Sec. III.B. */
+int lb_init(lb_ctx *c, const double *phi0, const double *u0, int ptr_kind);
+
+/* Advance nsteps (>= 0) timesteps, asynchronously on the context's stream.
+ * One timestep, per site x (all arithmetic in the context's precision):
+ *   phi = sum_i g_i;  d_a phi = (phi(x+e_a) - phi(x-e_a))/2;
+ *   lap phi = sum of the 6 face neighbours - 6 phi(x);
+ *   rho = sum_i f_i;  u = sum_i f_i c_i / rho;
+ *   mu = A phi + B phi^3 - kappa lap phi;
+ *   P_ab = [A/2 phi^2 + 3B/4 phi^4 - kappa phi lap phi - kappa/2 |grad phi|^2]
+ *          delta_ab + kappa d_a phi d_b phi;
+ *   feq_i = w_i [rho + 3 rho c_i.u + 9/2 (P + rho u u):(c_i c_i - I/3)];
+ *   geq_i = w_i [phi + 3 phi c_i.u
+ *               + 9/2 ((Gamma mu - phi/3) I + phi u u):(c_i c_i - I/3)];
+ *   f*_i = f_i - (f_i - feq_i)/tau;  g*_i = g_i - (g_i - geq_i)/tau_g;
+ *   f_i(x + c_i, t+1) = f*_i(x, t), likewise g (periodic wrap).
+ * Errors: LB_ERR_INVALID (c NULL, nsteps < 0), LB_ERR_CUDA.
+ * Paper: the binary-collision benchmark, Sec. IV; TARGET_LAUNCH, Sec. III.C. */
+int lb_step(lb_ctx *c, int nsteps);
+
+/* Moments of the current state: rho[N], u[3][N] (SoA, = sum f c / rho) and
+ * phi[N], written in FP64 to ptr_kind memory; any output may be NULL.
+ * LB_HOST synchronises the stream before returning.  Errors: LB_ERR_INVALID,
+ * LB_ERR_CUDA.  Paper: copyFromTarget, Sec. III.B. */
+int lb_moments(lb_ctx *c, double *rho, double *u, double *phi, int ptr_kind);
+
+/* Lattice totals out[5] = {sum rho, sum rho u_x, sum rho u_y, sum rho u_z,
+ * sum phi} (host array), accumulated in FP64 on the GPU in a fixed order
+ * (bitwise reproducible).  Synchronises the stream.  Returns
+ * LB_ERR_NONFINITE (with out filled) if any total is NaN or Inf.
+ * Paper: reductions are named as future work in Sec. V. */
+int lb_reduce(lb_ctx *c, double out[5]);
+
+/* Copy the full state out / in as post-streaming distributions f(x, t),
+ * g(x, t): double[19][N] each, in the ABI velocity order, ptr_kind memory.
+ * lb_get_state with LB_HOST synchronises.  These are the checkpoint /
+ * restart entry points.  Errors: LB_ERR_INVALID, LB_ERR_CUDA.
+ * Paper: copyFromTarget / copyToTarget, Sec. III.B. */
+int lb_get_state(lb_ctx *c, double *f, double *g, int ptr_kind);
+int lb_set_state(lb_ctx *c, const double *f, const double *g, int ptr_kind);
+
+/* Select the step kernel (LB_KERNEL_*) and its launch shape: block_x x
+ * block_y threads per CTA and z_chunk planes marched per CTA by the fused
+ * kernel (0 = library default for any of the three).  Validated against the
+ * kernel's limits; LB_ERR_INVALID otherwise.  Paper: the tunable VVL and TPB
+ * of TARGET_TLP / TARGET_LAUNCH, Sec. III.C. */
+int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk);
+
+/* Extents and precision of c (any output may be NULL). */
+int lb_get_info(const lb_ctx *c, int *nx, int *ny, int *nz, int *precision);
+
+/* Text of an LB_* code, and of the last CUDA error seen by this thread. */
+const char *lb_strerror(int code);
+const char *lb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_H */

@@ -1,0 +1,146 @@
+// d3q19.cuh -- D3Q19 velocity set and the per-site binary-fluid collision.
+//
+// The collision is the "binary collision" of targetDP Sec. IV: BGK
+// relaxation of the density distribution f toward an equilibrium whose
+// second moment carries the free-energy pressure tensor, and of the
+// order-parameter distribution g toward an equilibrium whose second moment is
+// Gamma*mu (symmetric free energy, Sec. II.A "free energy based approach").
+// Velocities come in opposite pairs (2k-1, 2k), so each equilibrium is
+// evaluated once per pair as (even part) +/- (odd part).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace lbk {
+
+constexpr int Q = 19;
+
+// ABI velocity order: 0 rest; 1..6 faces; 7..18 edges; odd/even = opposite.
+__host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr double weight(int i) {
+    return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// Relaxation and free-energy parameters in the arithmetic type T.
+template <typename T>
+struct Coll {
+    T omega, omega_g;      // 1/tau, 1/tau_g
+    T rho0;                // shift of the FP32 form
+    T gamma, A, B, kappa;
+};
+
+// Equilibria of f and g at one site.  R is rho (SH = false) or rho - rho0
+// (SH = true: the result is feq_i - w_i rho0).  j = sum f c = rho u.
+// sink(i, feq_i, geq_i) is called once per direction, i a literal after
+// inlining.
+template <typename T, bool SH, typename Sink>
+__device__ __forceinline__ void equilibria(const Coll<T>& p, T R, T jx, T jy, T jz,
+                                           T phi, T dx, T dy, T dz, T lap, Sink&& sink)
+{
+    const T third = T(1.0 / 3.0);
+    const T rho = SH ? p.rho0 + R : R;
+    const T rinv = T(1) / rho;
+    const T ux = jx * rinv, uy = jy * rinv, uz = jz * rinv;
+    const T phi2 = phi * phi;
+    const T mu = phi * (p.A + p.B * phi2) - p.kappa * lap;
+    const T pb = phi2 * (T(0.5) * p.A + T(0.75) * p.B * phi2)
+               - p.kappa * (phi * lap + T(0.5) * (dx * dx + dy * dy + dz * dz));
+    // S = P + rho u u
+    const T Sxx = pb + p.kappa * dx * dx + jx * ux;
+    const T Syy = pb + p.kappa * dy * dy + jy * uy;
+    const T Szz = pb + p.kappa * dz * dz + jz * uz;
+    const T Sxy = p.kappa * dx * dy + jx * uy;
+    const T Sxz = p.kappa * dx * dz + jx * uz;
+    const T Syz = p.kappa * dy * dz + jy * uz;
+    const T t3 = (Sxx + Syy + Szz) * third;
+    // g: G = (Gamma mu - phi/3) I + phi u u;  G:Q_i = phi (c.u)^2 - phi u^2/3 + (Gamma mu - phi/3)(c^2 - 1)
+    const T pu2 = phi * (ux * ux + uy * uy + uz * uz) * third;
+    const T gm = p.gamma * mu - phi * third;
+
+    const T w0 = T(1.0 / 3.0), w1 = T(1.0 / 18.0), w2 = T(1.0 / 36.0);
+    const T h = T(4.5), three = T(3);
+
+    sink(0, w0 * (R - h * t3), w0 * (phi - h * (pu2 + gm)));
+
+    // faces: S:Q = S_aa - t3
+    {
+        T fs = w1 * (R + h * (Sxx - t3)), fa = w1 * three * jx;
+        T gs = w1 * (phi + h * (phi * ux * ux - pu2)), ga = w1 * three * phi * ux;
+        sink(1, fs + fa, gs + ga); sink(2, fs - fa, gs - ga);
+    }
+    {
+        T fs = w1 * (R + h * (Syy - t3)), fa = w1 * three * jy;
+        T gs = w1 * (phi + h * (phi * uy * uy - pu2)), ga = w1 * three * phi * uy;
+        sink(3, fs + fa, gs + ga); sink(4, fs - fa, gs - ga);
+    }
+    {
+        T fs = w1 * (R + h * (Szz - t3)), fa = w1 * three * jz;
+        T gs = w1 * (phi + h * (phi * uz * uz - pu2)), ga = w1 * three * phi * uz;
+        sink(5, fs + fa, gs + ga); sink(6, fs - fa, gs - ga);
+    }
+    // edges: S:Q = S_aa + S_bb +/- 2 S_ab - t3
+#define LBK_EDGE(IP, IM, SAA, SBB, SAB, JA, JB, UA, UB, SGN)                          \
+    {                                                                                 \
+        const T cu = UA + SGN * UB;                                                   \
+        T fs = w2 * (R + h * (SAA + SBB + SGN * T(2) * SAB - t3));                    \
+        T fa = w2 * three * (JA + SGN * JB);                                          \
+        T gs = w2 * (phi + h * (phi * cu * cu - pu2 + gm));                           \
+        T ga = w2 * three * phi * cu;                                                 \
+        sink(IP, fs + fa, gs + ga); sink(IM, fs - fa, gs - ga);                       \
+    }
+    LBK_EDGE(7, 8, Sxx, Syy, Sxy, jx, jy, ux, uy, T(1))
+    LBK_EDGE(9, 10, Sxx, Syy, Sxy, jx, jy, ux, uy, T(-1))
+    LBK_EDGE(11, 12, Sxx, Szz, Sxz, jx, jz, ux, uz, T(1))
+    LBK_EDGE(13, 14, Sxx, Szz, Sxz, jx, jz, ux, uz, T(-1))
+    LBK_EDGE(15, 16, Syy, Szz, Syz, jy, jz, uy, uz, T(1))
+    LBK_EDGE(17, 18, Syy, Szz, Syz, jy, jz, uy, uz, T(-1))
+#undef LBK_EDGE
+}
+
+// Density moments of a (possibly shifted) distribution: R = sum f, j = sum f c.
+template <typename T>
+__device__ __forceinline__ void density_moments(const T (&f)[Q], T& R, T& jx, T& jy, T& jz)
+{
+    R = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))
+      + ((f[8] + f[9]) + (f[10] + f[11])) + ((f[12] + f[13]) + (f[14] + f[15]))
+      + ((f[16] + f[17]) + f[18]);
+    jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
+    jy = (f[3] - f[4]) + (f[7] - f[8]) - (f[9] - f[10]) + (f[15] - f[16]) + (f[17] - f[18]);
+    jz = (f[5] - f[6]) + (f[11] - f[12]) - (f[13] - f[14]) + (f[15] - f[16]) - (f[17] - f[18]);
+}
+
+template <typename T>
+__device__ __forceinline__ T sum19(const T (&g)[Q])
+{
+    return ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]))
+         + ((g[8] + g[9]) + (g[10] + g[11])) + ((g[12] + g[13]) + (g[14] + g[15]))
+         + ((g[16] + g[17]) + g[18]);
+}
+
+// In-place BGK collision of one site given phi and its stencil values.
+template <typename T, bool SH>
+__device__ __forceinline__ void collide(const Coll<T>& p, T (&f)[Q], T (&g)[Q],
+                                        T phi, T dx, T dy, T dz, T lap)
+{
+    T R, jx, jy, jz;
+    density_moments(f, R, jx, jy, jz);
+    const T om = p.omega, omg = p.omega_g;
+    equilibria<T, SH>(p, R, jx, jy, jz, phi, dx, dy, dz, lap,
+                      [&](int i, T feq, T geq) {
+                          f[i] = f[i] + om * (feq - f[i]);
+                          g[i] = g[i] + omg * (geq - g[i]);
+                      });
+}
+
+}  // namespace lbk

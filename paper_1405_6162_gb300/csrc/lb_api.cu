@@ -1,0 +1,317 @@
+// lb_api.cu -- the extern "C" entry points of liblb (declared in lb.h).
+//
+// The context owns the device-side lattice (the paper's "target copy",
+// targetDP Sec. III.A); every caller array is borrowed for the duration of
+// the call (host) or until the work queued on the context's stream has run
+// (device).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "d3q19.cuh"
+#include "lb_internal.cuh"
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+std::mutex g_alloc_mu;
+lb_alloc_fn g_alloc = nullptr;
+lb_free_fn g_free = nullptr;
+void *g_alloc_user = nullptr;
+
+void *dev_alloc(lb_ctx *c, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    if (c->alloc) return c->alloc(bytes, (void *)c->stream, c->alloc_user);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(lb_ctx *c, void *p, size_t bytes)
+{
+    if (!p) return;
+    if (bytes == 0) bytes = 256;
+    if (c->free_fn)
+        c->free_fn(p, bytes, (void *)c->stream, c->alloc_user);
+    else
+        cudaFree(p);
+}
+
+size_t dist_bytes(const lb_ctx *c) { return (size_t)lbk::Q * (size_t)c->N * c->esize; }
+size_t io_bytes(const lb_ctx *c) { return 5 * (size_t)c->N * sizeof(double); }
+
+void free_all(lb_ctx *c)
+{
+    for (int k = 0; k < 2; k++) {
+        dev_free(c, c->buf.f[k], dist_bytes(c));
+        dev_free(c, c->buf.g[k], dist_bytes(c));
+        c->buf.f[k] = c->buf.g[k] = nullptr;
+    }
+    dev_free(c, c->phi, (size_t)c->N * c->esize);
+    dev_free(c, c->io, io_bytes(c));
+    dev_free(c, c->partial, (size_t)lbk::kReduceBlocks * 5 * sizeof(double));
+    dev_free(c, c->dev_out, 8 * sizeof(double));
+    c->phi = nullptr;
+    c->io = nullptr;
+    c->partial = nullptr;
+    c->dev_out = nullptr;
+}
+
+bool finite_pos(double v) { return std::isfinite(v); }
+
+int validate(const lb_params *p)
+{
+    if (!p) return LB_ERR_INVALID;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return LB_ERR_INVALID;
+    const long long N = (long long)p->nx * p->ny * p->nz;
+    if (N >= (1LL << 31)) return LB_ERR_INVALID;
+    const double v[] = {p->tau, p->tau_g, p->rho0, p->gamma, p->A, p->B, p->kappa};
+    for (double x : v)
+        if (!finite_pos(x)) return LB_ERR_INVALID;
+    if (!(p->tau > 0.5) || !(p->tau_g > 0.5) || !(p->rho0 > 0.0)) return LB_ERR_INVALID;
+    if (p->precision != LB_FP64 && p->precision != LB_FP32_SHIFTED) return LB_ERR_INVALID;
+    return LB_OK;
+}
+
+int ensure_io(lb_ctx *c)
+{
+    if (c->io) return LB_OK;
+    c->io = (double *)dev_alloc(c, io_bytes(c));
+    return c->io ? LB_OK : LB_ERR_NOMEM;
+}
+
+int sync(lb_ctx *c) { return lbk::cuda_status(cudaStreamSynchronize(c->stream)); }
+
+int copy(lb_ctx *c, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind)
+{
+    if (bytes == 0) return LB_OK;
+    return lbk::cuda_status(cudaMemcpyAsync(dst, src, bytes, kind, c->stream));
+}
+
+}  // namespace
+
+namespace lbk {
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return LB_OK;
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LB_ERR_NOMEM : LB_ERR_CUDA;
+}
+
+int check_launch() { return cuda_status(cudaGetLastError()); }
+
+}  // namespace lbk
+
+extern "C" {
+
+const char *lb_strerror(int code)
+{
+    switch (code) {
+    case LB_OK: return "ok";
+    case LB_ERR_INVALID: return "invalid argument";
+    case LB_ERR_NOMEM: return "device allocation failed";
+    case LB_ERR_CUDA: return "CUDA error";
+    case LB_ERR_NONFINITE: return "non-finite value in the lattice state";
+    case LB_ERR_TIMEOUT: return "bounded device-side wait timed out";
+    default: return "unknown error code";
+    }
+}
+
+const char *lb_last_error(void) { return g_last_error; }
+
+int lb_set_allocator(lb_alloc_fn alloc, lb_free_fn free_fn, void *user)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) return LB_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_alloc_user = alloc ? user : nullptr;
+    return LB_OK;
+}
+
+int lb_create(const lb_params *p, void *cuda_stream, lb_ctx **out)
+{
+    if (!out) return LB_ERR_INVALID;
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc) return rc;
+    lb_ctx *c = new (std::nothrow) lb_ctx();
+    if (!c) return LB_ERR_NOMEM;
+    c->p = *p;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->N = (long long)p->nx * p->ny * p->nz;
+    c->esize = p->precision == LB_FP64 ? sizeof(double) : sizeof(float);
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        c->alloc = g_alloc;
+        c->free_fn = g_free;
+        c->alloc_user = g_alloc_user;
+    }
+    rc = lbk::cuda_status(cudaGetDevice(&c->device));
+    if (rc) {
+        delete c;
+        return rc;
+    }
+    for (int k = 0; k < 2; k++) {
+        c->buf.f[k] = dev_alloc(c, dist_bytes(c));
+        c->buf.g[k] = dev_alloc(c, dist_bytes(c));
+    }
+    c->phi = dev_alloc(c, (size_t)c->N * c->esize);
+    c->partial = (double *)dev_alloc(c, (size_t)lbk::kReduceBlocks * 5 * sizeof(double));
+    c->dev_out = (double *)dev_alloc(c, 8 * sizeof(double));
+    bool ok = c->phi && c->partial && c->dev_out;
+    for (int k = 0; k < 2; k++) ok = ok && c->buf.f[k] && c->buf.g[k];
+    if (!ok) {
+        free_all(c);
+        delete c;
+        return LB_ERR_NOMEM;
+    }
+    for (int k = 0; k < 2 && !rc; k++) {
+        rc = lbk::cuda_status(cudaMemsetAsync(c->buf.f[k], 0, dist_bytes(c), c->stream));
+        if (!rc) rc = lbk::cuda_status(cudaMemsetAsync(c->buf.g[k], 0, dist_bytes(c), c->stream));
+    }
+    if (rc) {
+        lb_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return LB_OK;
+}
+
+void lb_destroy(lb_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+}
+
+int lb_get_info(const lb_ctx *c, int *nx, int *ny, int *nz, int *precision)
+{
+    if (!c) return LB_ERR_INVALID;
+    if (nx) *nx = c->p.nx;
+    if (ny) *ny = c->p.ny;
+    if (nz) *nz = c->p.nz;
+    if (precision) *precision = c->p.precision;
+    return LB_OK;
+}
+
+int lb_init(lb_ctx *c, const double *phi0, const double *u0, int ptr_kind)
+{
+    if (!c || !phi0 || (ptr_kind != LB_HOST && ptr_kind != LB_DEVICE)) return LB_ERR_INVALID;
+    const size_t nb = (size_t)c->N * sizeof(double);
+    if (ptr_kind == LB_DEVICE) return lbk::launch_init(c, phi0, u0);
+    int rc = ensure_io(c);
+    if (rc) return rc;
+    rc = copy(c, c->io, phi0, nb, cudaMemcpyHostToDevice);
+    if (!rc && u0) rc = copy(c, c->io + c->N, u0, 3 * nb, cudaMemcpyHostToDevice);
+    if (!rc) rc = lbk::launch_init(c, c->io, u0 ? c->io + c->N : nullptr);
+    if (!rc) rc = sync(c);
+    return rc;
+}
+
+int lb_step(lb_ctx *c, int nsteps)
+{
+    if (!c || nsteps < 0) return LB_ERR_INVALID;
+    if (nsteps == 0) return LB_OK;
+    if (c->kernel == LB_KERNEL_TWO_PASS) return lbk::launch_step_two_pass(c, nsteps);
+    return lbk::launch_step_fused(c, nsteps);
+}
+
+int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk)
+{
+    if (!c) return LB_ERR_INVALID;
+    if (kernel != LB_KERNEL_AUTO && kernel != LB_KERNEL_TWO_PASS && kernel != LB_KERNEL_FUSED)
+        return LB_ERR_INVALID;
+    if (block_x < 0 || block_y < 0 || z_chunk < 0) return LB_ERR_INVALID;
+    if (kernel != LB_KERNEL_TWO_PASS) {
+        int rc = lbk::fused_validate(c->p.precision, block_x, block_y, z_chunk);
+        if (rc) return rc;
+    }
+    c->kernel = kernel;
+    c->block_x = block_x;
+    c->block_y = block_y;
+    c->z_chunk = z_chunk;
+    return LB_OK;
+}
+
+int lb_moments(lb_ctx *c, double *rho, double *u, double *phi, int ptr_kind)
+{
+    if (!c || (ptr_kind != LB_HOST && ptr_kind != LB_DEVICE)) return LB_ERR_INVALID;
+    if (!rho && !u && !phi) return LB_OK;
+    if (ptr_kind == LB_DEVICE) return lbk::launch_moments(c, rho, u, phi);
+    int rc = ensure_io(c);
+    if (rc) return rc;
+    const size_t N = (size_t)c->N, nb = N * sizeof(double);
+    rc = lbk::launch_moments(c, rho ? c->io : nullptr, u ? c->io + N : nullptr, phi ? c->io + 4 * N : nullptr);
+    if (!rc && rho) rc = copy(c, rho, c->io, nb, cudaMemcpyDeviceToHost);
+    if (!rc && u) rc = copy(c, u, c->io + N, 3 * nb, cudaMemcpyDeviceToHost);
+    if (!rc && phi) rc = copy(c, phi, c->io + 4 * N, nb, cudaMemcpyDeviceToHost);
+    if (!rc) rc = sync(c);
+    return rc;
+}
+
+int lb_reduce(lb_ctx *c, double out[5])
+{
+    if (!c || !out) return LB_ERR_INVALID;
+    int rc = lbk::launch_reduce(c, c->dev_out);
+    if (!rc) rc = copy(c, out, c->dev_out, 5 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (!rc) rc = sync(c);
+    if (rc) return rc;
+    for (int k = 0; k < 5; k++)
+        if (!std::isfinite(out[k])) return LB_ERR_NONFINITE;
+    return LB_OK;
+}
+
+int lb_get_state(lb_ctx *c, double *f, double *g, int ptr_kind)
+{
+    if (!c || (ptr_kind != LB_HOST && ptr_kind != LB_DEVICE)) return LB_ERR_INVALID;
+    if (ptr_kind == LB_DEVICE) return lbk::launch_get_state(c, f, g);
+    int rc = ensure_io(c);
+    if (rc) return rc;
+    const size_t N = (size_t)c->N;
+    double *dst[2] = {f, g};
+    for (int which = 0; which < 2 && !rc; which++) {
+        if (!dst[which]) continue;
+        for (int i0 = 0; i0 < lbk::Q && !rc; i0 += 5) {
+            const int i1 = i0 + 5 < lbk::Q ? i0 + 5 : lbk::Q;
+            rc = lbk::launch_rows(c, which, i0, i1, c->io, 0);
+            if (!rc) rc = copy(c, dst[which] + (size_t)i0 * N, c->io, (size_t)(i1 - i0) * N * sizeof(double),
+                               cudaMemcpyDeviceToHost);
+            if (!rc) rc = sync(c);
+        }
+    }
+    return rc;
+}
+
+int lb_set_state(lb_ctx *c, const double *f, const double *g, int ptr_kind)
+{
+    if (!c || (ptr_kind != LB_HOST && ptr_kind != LB_DEVICE)) return LB_ERR_INVALID;
+    if (ptr_kind == LB_DEVICE) return lbk::launch_set_state(c, f, g);
+    int rc = ensure_io(c);
+    if (rc) return rc;
+    const size_t N = (size_t)c->N;
+    const double *src[2] = {f, g};
+    for (int which = 0; which < 2 && !rc; which++) {
+        if (!src[which]) continue;
+        for (int i0 = 0; i0 < lbk::Q && !rc; i0 += 5) {
+            const int i1 = i0 + 5 < lbk::Q ? i0 + 5 : lbk::Q;
+            rc = copy(c, c->io, src[which] + (size_t)i0 * N, (size_t)(i1 - i0) * N * sizeof(double),
+                      cudaMemcpyHostToDevice);
+            if (!rc) rc = lbk::launch_rows(c, which, i0, i1, c->io, 1);
+            if (!rc) rc = sync(c);
+        }
+    }
+    return rc;
+}
+
+}  // extern "C"

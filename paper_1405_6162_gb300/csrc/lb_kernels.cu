@@ -1,0 +1,403 @@
+// lb_kernels.cu -- initialisation, two-pass timestep, moments, state I/O and
+// the FP64 conservation reductions.
+//
+// Storage convention: the context keeps the post-collision, pre-streaming
+// distributions A_i(x).  The post-streaming state of the model is the pull
+// f_i(x, t) = A_i(x - c_i), so one timestep is "pull, collide at x, write
+// A'_i(x)": every store is aligned to its own site and every load is a
+// shifted, still coalesced read (targetDP Sec. III.B: SoA so consecutive
+// sites are consecutive in memory).
+#include <cuda_runtime.h>
+
+#include "d3q19.cuh"
+#include "lb_internal.cuh"
+
+namespace lbk {
+
+// Periodic neighbourhood of site s: X[k], Y[k], Z[k] are the coordinates
+// x + k - 1 (wrapped), pre-multiplied by the row and plane strides.
+struct Nbr {
+    int X[3], Y[3], Z[3];
+    __device__ __forceinline__ Nbr(int s, int nx, int ny, int nz)
+    {
+        const int x = s % nx;
+        const int r = s / nx;
+        const int y = r % ny;
+        const int z = r / ny;
+        X[0] = (x == 0 ? nx : x) - 1; X[1] = x; X[2] = (x + 1 == nx) ? 0 : x + 1;
+        Y[0] = ((y == 0 ? ny : y) - 1) * nx; Y[1] = y * nx; Y[2] = ((y + 1 == ny) ? 0 : y + 1) * nx;
+        const int pl = nx * ny;
+        Z[0] = ((z == 0 ? nz : z) - 1) * pl; Z[1] = z * pl; Z[2] = ((z + 1 == nz) ? 0 : z + 1) * pl;
+    }
+    __device__ __forceinline__ int at(int ox, int oy, int oz) const
+    {
+        return X[ox + 1] + Y[oy + 1] + Z[oz + 1];
+    }
+    // site the pull of direction i reads from: x - c_i
+    __device__ __forceinline__ int src(int i) const { return at(-cx(i), -cy(i), -cz(i)); }
+};
+
+template <typename T>
+Coll<T> make_coll(const lb_params &p)
+{
+    Coll<T> c;
+    c.omega = T(1.0 / p.tau);
+    c.omega_g = T(1.0 / p.tau_g);
+    c.rho0 = T(p.rho0);
+    c.gamma = T(p.gamma);
+    c.A = T(p.A);
+    c.B = T(p.B);
+    c.kappa = T(p.kappa);
+    return c;
+}
+
+template <typename T>
+__device__ __forceinline__ void stencil(const T *__restrict__ phi, const Nbr &n, T ph,
+                                        T &dx, T &dy, T &dz, T &lap)
+{
+    const T xp = phi[n.at(1, 0, 0)], xm = phi[n.at(-1, 0, 0)];
+    const T yp = phi[n.at(0, 1, 0)], ym = phi[n.at(0, -1, 0)];
+    const T zp = phi[n.at(0, 0, 1)], zm = phi[n.at(0, 0, -1)];
+    dx = T(0.5) * (xp - xm);
+    dy = T(0.5) * (yp - ym);
+    dz = T(0.5) * (zp - zm);
+    lap = ((xp + xm) + (yp + ym)) + (zp + zm) - T(6) * ph;
+}
+
+// ------------------------------------------------------------------ init
+
+template <typename T, bool SH>
+__global__ void __launch_bounds__(256) k_init(const double *__restrict__ phi0,
+                                              const double *__restrict__ u0,
+                                              T *__restrict__ fa, T *__restrict__ ga,
+                                              Coll<double> p, int nx, int ny, int nz)
+{
+    const long long N = (long long)nx * ny * nz;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const Nbr n(s, nx, ny, nz);
+    const double ph = phi0[s];
+    double dx, dy, dz, lap;
+    stencil(phi0, n, ph, dx, dy, dz, lap);
+    const double jx = u0 ? p.rho0 * u0[s] : 0.0;
+    const double jy = u0 ? p.rho0 * u0[N + s] : 0.0;
+    const double jz = u0 ? p.rho0 * u0[2 * N + s] : 0.0;
+    const double R = SH ? 0.0 : p.rho0;
+    // A_i(x - c_i) = feq_i(x): the first pull then yields the equilibrium.
+    equilibria<double, SH>(p, R, jx, jy, jz, ph, dx, dy, dz, lap,
+                           [&](int i, double fe, double ge) {
+                               const size_t o = (size_t)i * N + n.src(i);
+                               fa[o] = T(fe);
+                               ga[o] = T(ge);
+                           });
+}
+
+// ------------------------------------------------------------------ two-pass step
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_phi_pull(const T *__restrict__ ga, T *__restrict__ phi,
+                                                  int nx, int ny, int nz)
+{
+    const long long N = (long long)nx * ny * nz;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const Nbr n(s, nx, ny, nz);
+    T g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) g[i] = ga[(size_t)i * N + n.src(i)];
+    phi[s] = sum19(g);
+}
+
+template <typename T, bool SH>
+__global__ void __launch_bounds__(256) k_collide_pull(const T *__restrict__ fa, const T *__restrict__ ga,
+                                                      const T *__restrict__ phi,
+                                                      T *__restrict__ fb, T *__restrict__ gb,
+                                                      Coll<T> p, int nx, int ny, int nz)
+{
+    const long long N = (long long)nx * ny * nz;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const Nbr n(s, nx, ny, nz);
+    T f[Q], g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const size_t o = (size_t)i * N + n.src(i);
+        f[i] = fa[o];
+        g[i] = ga[o];
+    }
+    const T ph = phi[s];
+    T dx, dy, dz, lap;
+    stencil(phi, n, ph, dx, dy, dz, lap);
+    collide<T, SH>(p, f, g, ph, dx, dy, dz, lap);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        fb[(size_t)i * N + s] = f[i];
+        gb[(size_t)i * N + s] = g[i];
+    }
+}
+
+// ------------------------------------------------------------------ moments / state
+
+template <typename T, bool SH>
+__global__ void __launch_bounds__(256) k_moments(const T *__restrict__ fa, const T *__restrict__ ga,
+                                                 double *__restrict__ rho, double *__restrict__ u,
+                                                 double *__restrict__ phi, double rho0,
+                                                 int nx, int ny, int nz)
+{
+    const long long N = (long long)nx * ny * nz;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const Nbr n(s, nx, ny, nz);
+    double f[Q], g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const size_t o = (size_t)i * N + n.src(i);
+        f[i] = double(fa[o]);
+        g[i] = double(ga[o]);
+    }
+    double R, jx, jy, jz;
+    density_moments(f, R, jx, jy, jz);
+    const double r = SH ? rho0 + R : R;
+    if (rho) rho[s] = r;
+    if (u) {
+        u[s] = jx / r;
+        u[N + s] = jy / r;
+        u[2 * N + s] = jz / r;
+    }
+    if (phi) phi[s] = sum19(g);
+}
+
+// out[(i - i0)*N + s] = A_i(x - c_i) + shift_i, for i in [i0, i1)
+template <typename T>
+__global__ void __launch_bounds__(256) k_get_state(const T *__restrict__ a, double *__restrict__ out,
+                                                   int i0, int i1, double shift_rho0,
+                                                   int nx, int ny, int nz)
+{
+    const long long N = (long long)nx * ny * nz;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const Nbr n(s, nx, ny, nz);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        if (i < i0 || i >= i1) continue;
+        out[(size_t)(i - i0) * N + s] = double(a[(size_t)i * N + n.src(i)]) + weight(i) * shift_rho0;
+    }
+}
+
+// A_i(x - c_i) = in[(i - i0)*N + s] - shift_i, for i in [i0, i1)
+template <typename T>
+__global__ void __launch_bounds__(256) k_set_state(T *__restrict__ a, const double *__restrict__ in,
+                                                   int i0, int i1, double shift_rho0,
+                                                   int nx, int ny, int nz)
+{
+    const long long N = (long long)nx * ny * nz;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const Nbr n(s, nx, ny, nz);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        if (i < i0 || i >= i1) continue;
+        a[(size_t)i * N + n.src(i)] = T(in[(size_t)(i - i0) * N + s] - weight(i) * shift_rho0);
+    }
+}
+
+// ------------------------------------------------------------------ reductions
+// Totals over all sites need no pull: sum_x f_i(x, t) = sum_x A_i(x - c_i)
+// = sum_x A_i(x) on the periodic lattice.
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int K>
+__device__ __forceinline__ void block_sum(double (&acc)[K], double *out)
+{
+    __shared__ double sh[kReduceThreads / 32][K];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; k++) acc[k] = warp_sum(acc[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; k++) sh[wid][k] = acc[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            double v = lane < kReduceThreads / 32 ? sh[lane][k] : 0.0;
+            v = warp_sum(v);
+            if (lane == 0) out[k] = v;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_partial(const T *__restrict__ fa,
+                                                                   const T *__restrict__ ga,
+                                                                   long long N, double *__restrict__ partial)
+{
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < N;
+         s += (long long)gridDim.x * blockDim.x) {
+        double f[Q], g[Q];
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            f[i] = double(fa[(size_t)i * N + s]);
+            g[i] = double(ga[(size_t)i * N + s]);
+        }
+        double R, jx, jy, jz;
+        density_moments(f, R, jx, jy, jz);
+        acc[0] += R;
+        acc[1] += jx;
+        acc[2] += jy;
+        acc[3] += jz;
+        acc[4] += sum19(g);
+    }
+    block_sum<5>(acc, partial + 5 * blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_final(const double *__restrict__ partial,
+                                                                 int nblocks, double offset0,
+                                                                 double *__restrict__ out)
+{
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 5; k++) acc[k] += partial[5 * b + k];
+    __shared__ double res[5];
+    block_sum<5>(acc, res);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        out[0] = res[0] + offset0;
+        for (int k = 1; k < 5; k++) out[k] = res[k];
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+
+static inline unsigned grid_for(long long N, int tpb) { return (unsigned)((N + tpb - 1) / tpb); }
+
+int launch_init(lb_ctx *c, const double *phi0_d, const double *u0_d)
+{
+    const auto p = make_coll<double>(c->p);
+    const int cur = c->buf.cur;
+    const unsigned grid = grid_for(c->N, 256);
+    if (c->p.precision == LB_FP64)
+        k_init<double, false><<<grid, 256, 0, c->stream>>>(phi0_d, u0_d, (double *)c->buf.f[cur],
+                                                           (double *)c->buf.g[cur], p, c->p.nx, c->p.ny, c->p.nz);
+    else
+        k_init<float, true><<<grid, 256, 0, c->stream>>>(phi0_d, u0_d, (float *)c->buf.f[cur],
+                                                         (float *)c->buf.g[cur], p, c->p.nx, c->p.ny, c->p.nz);
+    return check_launch();
+}
+
+template <typename T, bool SH>
+static int two_pass(lb_ctx *c, int nsteps)
+{
+    const auto p = make_coll<T>(c->p);
+    const unsigned grid = grid_for(c->N, 256);
+    const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    for (int t = 0; t < nsteps; t++) {
+        const int a = c->buf.cur, b = 1 - a;
+        k_phi_pull<T><<<grid, 256, 0, c->stream>>>((const T *)c->buf.g[a], (T *)c->phi, nx, ny, nz);
+        k_collide_pull<T, SH><<<grid, 256, 0, c->stream>>>((const T *)c->buf.f[a], (const T *)c->buf.g[a],
+                                                           (const T *)c->phi, (T *)c->buf.f[b],
+                                                           (T *)c->buf.g[b], p, nx, ny, nz);
+        int rc = check_launch();
+        if (rc) return rc;
+        c->buf.cur = b;
+    }
+    return LB_OK;
+}
+
+int launch_step_two_pass(lb_ctx *c, int nsteps)
+{
+    return c->p.precision == LB_FP64 ? two_pass<double, false>(c, nsteps) : two_pass<float, true>(c, nsteps);
+}
+
+int launch_moments(lb_ctx *c, double *rho, double *u, double *phi)
+{
+    const int cur = c->buf.cur;
+    const unsigned grid = grid_for(c->N, 256);
+    if (c->p.precision == LB_FP64)
+        k_moments<double, false><<<grid, 256, 0, c->stream>>>((const double *)c->buf.f[cur],
+                                                              (const double *)c->buf.g[cur], rho, u, phi,
+                                                              c->p.rho0, c->p.nx, c->p.ny, c->p.nz);
+    else
+        k_moments<float, true><<<grid, 256, 0, c->stream>>>((const float *)c->buf.f[cur],
+                                                            (const float *)c->buf.g[cur], rho, u, phi,
+                                                            c->p.rho0, c->p.nx, c->p.ny, c->p.nz);
+    return check_launch();
+}
+
+// f or g, components [i0, i1), to out (i1 - i0 rows of N)
+static int get_rows(lb_ctx *c, int which, int i0, int i1, double *out)
+{
+    const int cur = c->buf.cur;
+    const unsigned grid = grid_for(c->N, 256);
+    const double shift = (which == 0 && c->p.precision == LB_FP32_SHIFTED) ? c->p.rho0 : 0.0;
+    void *a = which == 0 ? c->buf.f[cur] : c->buf.g[cur];
+    if (c->p.precision == LB_FP64)
+        k_get_state<double><<<grid, 256, 0, c->stream>>>((const double *)a, out, i0, i1, shift,
+                                                         c->p.nx, c->p.ny, c->p.nz);
+    else
+        k_get_state<float><<<grid, 256, 0, c->stream>>>((const float *)a, out, i0, i1, shift,
+                                                        c->p.nx, c->p.ny, c->p.nz);
+    return check_launch();
+}
+
+static int set_rows(lb_ctx *c, int which, int i0, int i1, const double *in)
+{
+    const int cur = c->buf.cur;
+    const unsigned grid = grid_for(c->N, 256);
+    const double shift = (which == 0 && c->p.precision == LB_FP32_SHIFTED) ? c->p.rho0 : 0.0;
+    void *a = which == 0 ? c->buf.f[cur] : c->buf.g[cur];
+    if (c->p.precision == LB_FP64)
+        k_set_state<double><<<grid, 256, 0, c->stream>>>((double *)a, in, i0, i1, shift,
+                                                         c->p.nx, c->p.ny, c->p.nz);
+    else
+        k_set_state<float><<<grid, 256, 0, c->stream>>>((float *)a, in, i0, i1, shift,
+                                                        c->p.nx, c->p.ny, c->p.nz);
+    return check_launch();
+}
+
+int launch_get_state(lb_ctx *c, double *f, double *g)
+{
+    int rc = LB_OK;
+    if (f) rc = get_rows(c, 0, 0, Q, f);
+    if (!rc && g) rc = get_rows(c, 1, 0, Q, g);
+    return rc;
+}
+
+int launch_set_state(lb_ctx *c, const double *f, const double *g)
+{
+    int rc = LB_OK;
+    if (f) rc = set_rows(c, 0, 0, Q, f);
+    if (!rc && g) rc = set_rows(c, 1, 0, Q, g);
+    return rc;
+}
+
+int launch_rows(lb_ctx *c, int which, int i0, int i1, double *buf, int dir)
+{
+    return dir == 0 ? get_rows(c, which, i0, i1, buf) : set_rows(c, which, i0, i1, buf);
+}
+
+int launch_reduce(lb_ctx *c, double *dev_out5)
+{
+    const int cur = c->buf.cur;
+    const double off = c->p.precision == LB_FP32_SHIFTED ? double(c->N) * c->p.rho0 : 0.0;
+    if (c->p.precision == LB_FP64)
+        k_reduce_partial<double><<<kReduceBlocks, kReduceThreads, 0, c->stream>>>(
+            (const double *)c->buf.f[cur], (const double *)c->buf.g[cur], c->N, c->partial);
+    else
+        k_reduce_partial<float><<<kReduceBlocks, kReduceThreads, 0, c->stream>>>(
+            (const float *)c->buf.f[cur], (const float *)c->buf.g[cur], c->N, c->partial);
+    int rc = check_launch();
+    if (rc) return rc;
+    k_reduce_final<<<1, kReduceThreads, 0, c->stream>>>(c->partial, kReduceBlocks, off, dev_out5);
+    return check_launch();
+}
+
+}  // namespace lbk

@@ -1,0 +1,123 @@
+"""Full-size (256^3) checks in the launch configuration the benchmark times.
+
+The oracle cannot step a 256^3 lattice in seconds, so these use facts that
+hold at any size:
+* a field uniform in y and z evolves exactly like the 256 x 1 x 1 lattice
+  (the y/z stencils and streaming wrap onto the same site), so every site of
+  the GPU result is compared with the 1-D oracle;
+* one step of a site depends only on the 5^3 neighbourhood around it, so
+  sampled sites of a random full-size state are checked against the oracle
+  run on that neighbourhood.
+"""
+import numpy as np
+import pytest
+
+import lb_inputs as L
+import oracle
+from tests.parity import P0, TOL_FP64, abi_order, rel
+
+pytestmark = pytest.mark.gpu
+
+FULL = (256, 256, 256)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    import paper_1405_6162_gb300 as lbpkg
+    lbpkg.build()
+    oracle.build()
+
+
+def _bench_lattice(params, precision):
+    from paper_1405_6162_gb300 import Lattice, tuning
+    lat = Lattice.from_params(FULL, params, precision=precision)
+    lat.set_kernel(*tuning.bench_config(FULL, precision))
+    return lat
+
+
+def _one_d(params, phi_line, u_line, nsteps):
+    d1 = (FULL[0], 1, 1)
+    f, g = oracle.step(d1, params, *oracle.init(d1, params, phi_line, u_line), nsteps)
+    return oracle.moments(d1, f, g)
+
+
+def _broadcast(line):
+    return np.broadcast_to(line, (FULL[2] * FULL[1], FULL[0])).reshape(-1)
+
+
+# FP32-shifted vs the FP64 oracle over these step counts, max-norm scaled
+TOL_FP32_1D = {"rho": 1e-6, "u": 1e-4, "phi": 1e-5}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_shifted"])
+@pytest.mark.parametrize("amplitude", [1.0, 0.5])
+def test_flat_interface_256cubed_equals_1d_oracle(precision, amplitude):
+    nsteps = 40
+    xi = L.interface_width(P0["A"], P0["kappa"])
+    line = L.flat_interface_phi0(FULL[0], 1, 1, amplitude, xi)
+    want = _one_d(P0, line, None, nsteps)
+    with _bench_lattice(P0, precision) as lat:
+        lat.init(_broadcast(line))
+        lat.step(nsteps)
+        rho, u, phi = lat.moments()
+    for name, a, b in (("rho", rho, want[0]), ("phi", phi, want[2])):
+        e = rel(a.reshape(-1, FULL[0]), b[None, :])
+        tol = TOL_FP64 if precision == "fp64" else TOL_FP32_1D[name]
+        assert e <= tol, (name, e)
+    ux = u[0].reshape(-1, FULL[0])
+    e = rel(ux, want[1][0][None, :])
+    assert e <= (TOL_FP64 if precision == "fp64" else TOL_FP32_1D["u"]), ("u", e)
+    assert np.abs(u[1:]).max() == 0.0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_shifted"])
+@pytest.mark.parametrize("tau", [0.6, 1.0])
+def test_shear_wave_256cubed_equals_1d_oracle(precision, tau):
+    nsteps = 30
+    p = dict(P0, tau=tau)
+    u_line = L.shear_wave_u0(FULL[0], 1, 1, amp=0.01)
+    want = _one_d(p, np.zeros(FULL[0]), u_line, nsteps)
+    with _bench_lattice(p, precision) as lat:
+        lat.init(np.zeros(int(np.prod(FULL))), np.stack([_broadcast(u_line[a]) for a in range(3)]))
+        lat.step(nsteps)
+        rho, u, phi = lat.moments()
+    tol = TOL_FP64 if precision == "fp64" else TOL_FP32_1D["u"]
+    assert rel(u[1].reshape(-1, FULL[0]), want[1][1][None, :]) <= tol
+    assert np.abs(phi).max() == 0.0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_shifted"])
+def test_sampled_sites_one_step_256cubed(precision):
+    import torch
+    from paper_1405_6162_gb300 import Lattice, tuning  # noqa: F401
+    n = int(np.prod(FULL))
+    nx, ny, nz = FULL
+    phi0 = L.spinodal_phi0(*FULL, seed=90, amp=0.8)
+    u0 = 0.02 * L.uniform(91, 3 * n, -1, 1).reshape(3, n)
+    o2a = abi_order()
+    with _bench_lattice(P0, precision) as lat:
+        lat.init(phi0, u0)
+        lat.step(3)                                     # move away from equilibrium
+        f0, g0 = lat.get_state(device=True)
+        lat.step(1)
+        f1, g1 = lat.get_state(device=True)
+        torch.cuda.synchronize()
+        sites = L.uniform_int(92, 48, 0, n - 1)
+        off = np.arange(-2, 3)
+        oz, oy, ox = np.meshgrid(off, off, off, indexing="ij")
+        for s in sites:
+            x, y, z = s % nx, (s // nx) % ny, s // (nx * ny)
+            nb = ((x + ox) % nx + nx * (((y + oy) % ny) + ny * ((z + oz) % nz))).reshape(-1)
+            idx = torch.from_numpy(nb).cuda()
+            fb = f0[:, idx].cpu().numpy()[o2a]          # 5^3 box, oracle order
+            gb = g0[:, idx].cpu().numpy()[o2a]
+            fo, go = oracle.step((5, 5, 5), P0, fb, gb, 1)
+            centre = 2 + 5 * (2 + 5 * 2)
+            fg = f1[:, int(s)].cpu().numpy()[o2a]
+            gg = g1[:, int(s)].cpu().numpy()[o2a]
+            if precision == "fp64":
+                assert np.abs(fg - fo[:, centre]).max() <= 1e-14
+                assert np.abs(gg - go[:, centre]).max() <= 1e-14
+            else:
+                assert np.abs(fg - fo[:, centre]).max() <= 2e-8
+                assert np.abs(gg - go[:, centre]).max() <= 2e-7

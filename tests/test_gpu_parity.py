@@ -1,0 +1,201 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+FP64: every field within 1e-12 of the oracle (max-norm scaled) after N
+steps.  FP32-shifted: float storage and arithmetic of f_i - w_i rho0 and g_i;
+its tolerance is stated per test from the arithmetic (float rounding of
+O(1e-2) distribution values, accumulated over the steps run).
+"""
+import numpy as np
+import pytest
+
+import lb_inputs as L
+import oracle
+from tests.parity import (P0, TOL_FP64, gpu_lattice, nonequilibrium_state, rel, to_abi,
+                          to_oracle)
+
+pytestmark = pytest.mark.gpu
+
+KERNEL_CASES = [("two_pass", (0, 0, 0)), ("fused", (0, 0, 0)), ("fused", (64, 2, 5)),
+                ("fused", (32, 1, 1)), ("fused", (128, 4, 7))]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    import paper_1405_6162_gb300 as lbpkg
+    lbpkg.build()
+    oracle.build()
+
+
+def _oracle_run(dims, params, f, g, nsteps):
+    f2, g2 = oracle.step(dims, params, f, g, nsteps)
+    return (f2, g2), oracle.moments(dims, f2, g2)
+
+
+def _check_moments(got, want, tol):
+    for name, a, b in zip(("rho", "u", "phi"), got, want):
+        e = rel(a, b)
+        assert e <= tol, f"{name}: {e:.3e} > {tol:.1e}"
+
+
+# ------------------------------------------------------------------ FP64
+
+@pytest.mark.parametrize("kernel,block", KERNEL_CASES)
+def test_spinodal_32cubed_fp64(kernel, block):
+    """32^3, 10 steps, phi0 ~ U[-0.01, 0.01] seed 0, f and g at equilibrium."""
+    dims = (32, 32, 32)
+    phi0 = L.spinodal_phi0(*dims, seed=0)
+    f0, g0 = oracle.init(dims, P0, phi0)
+    (fo, go), mo = _oracle_run(dims, P0, f0, g0, 10)
+    with gpu_lattice(dims, P0, "fp64", kernel, block) as lat:
+        lat.init(phi0)
+        lat.step(10)
+        _check_moments(lat.moments(), mo, TOL_FP64)
+        f, g = lat.get_state()
+    assert rel(to_oracle(f), fo) <= TOL_FP64
+    assert rel(to_oracle(g), go) <= TOL_FP64
+
+
+RAGGED = [(13, 7, 5), (1, 1, 9), (33, 1, 2), (5, 17, 1), (40, 9, 35), (1, 1, 1), (2, 3, 2)]
+
+
+@pytest.mark.parametrize("dims", RAGGED)
+@pytest.mark.parametrize("kernel,block", KERNEL_CASES)
+def test_ragged_nonequilibrium_fp64(dims, kernel, block):
+    p = dict(P0, tau=0.7, tau_g=0.9, kappa=0.06)
+    f0, g0 = nonequilibrium_state(dims, p, seed=31)
+    (fo, go), mo = _oracle_run(dims, p, f0, g0, 4)
+    with gpu_lattice(dims, p, "fp64", kernel, block) as lat:
+        lat.set_state(to_abi(f0), to_abi(g0))
+        lat.step(4)
+        _check_moments(lat.moments(), mo, TOL_FP64)
+        f, g = lat.get_state()
+    assert rel(to_oracle(f), fo) <= TOL_FP64
+    assert rel(to_oracle(g), go) <= TOL_FP64
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_shifted"])
+def test_fused_and_two_pass_bitwise_identical(precision):
+    dims = (48, 20, 17)
+    p = dict(P0, tau=0.8)
+    f0, g0 = nonequilibrium_state(dims, p, seed=41)
+    out = []
+    for kernel, block in (("two_pass", (0, 0, 0)), ("fused", (32, 4, 6)), ("fused", (64, 8, 32))):
+        with gpu_lattice(dims, p, precision, kernel, block) as lat:
+            lat.set_state(to_abi(f0), to_abi(g0))
+            lat.step(6)
+            out.append(lat.get_state())
+    for f, g in out[1:]:
+        assert np.array_equal(f, out[0][0]) and np.array_equal(g, out[0][1])
+
+
+def test_init_with_flow_matches_oracle():
+    dims = (12, 10, 8)
+    n = 960
+    phi0 = L.spinodal_phi0(*dims, seed=5, amp=0.4)
+    u0 = 0.03 * L.uniform(6, 3 * n, -1, 1).reshape(3, n)
+    fo, go = oracle.init(dims, P0, phi0, u0)
+    with gpu_lattice(dims, P0, "fp64") as lat:
+        lat.init(phi0, u0)
+        f, g = lat.get_state()
+        rho, u, phi = lat.moments()
+    assert rel(to_oracle(f), fo) <= 1e-15 and rel(to_oracle(g), go) <= 1e-15
+    assert np.abs(rho - 1).max() < 1e-15
+    assert rel(u, u0) < 1e-14 and rel(phi, phi0) < 1e-15
+
+
+def test_device_pointer_inputs_and_outputs():
+    import torch
+    dims = (16, 8, 4)
+    phi0 = L.spinodal_phi0(*dims, seed=8, amp=0.2)
+    (fo, go), mo = _oracle_run(dims, P0, *oracle.init(dims, P0, phi0), 3)
+    with gpu_lattice(dims, P0, "fp64") as lat:
+        lat.init(torch.from_numpy(phi0).cuda())
+        lat.step(3)
+        rho, u, phi = lat.moments(device=True)
+        f, g = lat.get_state(device=True)
+        torch.cuda.synchronize()
+    _check_moments((rho.cpu().numpy(), u.cpu().numpy(), phi.cpu().numpy()), mo, TOL_FP64)
+    assert rel(to_oracle(f.cpu().numpy()), fo) <= TOL_FP64
+
+
+def test_state_roundtrip_exact_fp64():
+    dims = (7, 6, 5)
+    f0, g0 = nonequilibrium_state(dims, P0, seed=50)
+    with gpu_lattice(dims, P0, "fp64") as lat:
+        lat.set_state(to_abi(f0), to_abi(g0))
+        f, g = lat.get_state()
+    assert np.array_equal(to_oracle(f), f0) and np.array_equal(to_oracle(g), g0)
+
+
+def test_reductions_match_oracle_and_conserve():
+    dims = (24, 20, 16)
+    p = dict(P0, tau=0.75)
+    f0, g0 = nonequilibrium_state(dims, p, seed=60)
+    r_or = oracle.reduce(dims, f0, g0)
+    with gpu_lattice(dims, p, "fp64") as lat:
+        lat.set_state(to_abi(f0), to_abi(g0))
+        r0 = lat.reduce()
+        lat.step(200)
+        r1 = lat.reduce()
+        r1b = lat.reduce()
+    assert np.abs(r0 - r_or).max() <= 1e-12 * abs(r_or[0])
+    assert np.array_equal(r1, r1b)                      # fixed-order sums
+    assert abs(r1[0] - r0[0]) <= 1e-13 * r0[0]
+    assert np.abs(r1[1:] - r0[1:]).max() <= 1e-13 * r0[0]
+
+
+def test_nonfinite_state_is_reported():
+    from paper_1405_6162_gb300 import LBError
+    from paper_1405_6162_gb300 import _lib as LL
+    dims = (8, 8, 8)
+    f0, g0 = nonequilibrium_state(dims, P0, seed=70)
+    f0[3, 100] = np.nan
+    for precision in ("fp64", "fp32_shifted"):
+        with gpu_lattice(dims, P0, precision) as lat:
+            lat.set_state(to_abi(f0), to_abi(g0))
+            with pytest.raises(LBError) as ei:
+                lat.reduce()
+            assert ei.value.code == LL.LB_ERR_NONFINITE
+            lat.step(1)       # the context stays usable after the report
+
+
+# ------------------------------------------------------------------ FP32 shifted
+
+# Float rounding of the shifted values (|f - w rho0| <~ 1e-2, ulp ~ 1e-9) and
+# of g (|g| <~ 0.5, ulp ~ 3e-8) per step, over 10 steps, relative to each
+# field's max-norm.
+TOL_FP32 = {"rho": 2e-7, "u": 1e-4, "phi": 1e-5}
+
+
+@pytest.mark.parametrize("kernel,block", KERNEL_CASES[:3])
+def test_spinodal_32cubed_fp32_shifted(kernel, block):
+    dims = (32, 32, 32)
+    phi0 = L.spinodal_phi0(*dims, seed=0)
+    (fo, go), mo = _oracle_run(dims, P0, *oracle.init(dims, P0, phi0), 10)
+    with gpu_lattice(dims, P0, "fp32_shifted", kernel, block) as lat:
+        lat.init(phi0)
+        lat.step(10)
+        got = lat.moments()
+    errs = {k: rel(a, b) for k, a, b in zip(("rho", "u", "phi"), got, mo)}
+    print("fp32-shifted 32^3 x 10 errors:", errs)
+    for k, e in errs.items():
+        assert e <= TOL_FP32[k], (k, e)
+
+
+@pytest.mark.parametrize("dims", [(13, 7, 5), (40, 9, 35), (1, 1, 3)])
+def test_ragged_fp32_shifted_one_step(dims):
+    """One step from a float-representable state: the only difference from
+    the FP64 oracle is float arithmetic within the step."""
+    p = dict(P0, tau=0.7)
+    f0, g0 = nonequilibrium_state(dims, p, seed=80)
+    with gpu_lattice(dims, p, "fp32_shifted", "fused", (32, 2, 3)) as lat:
+        lat.set_state(to_abi(f0), to_abi(g0))
+        fin, gin = lat.get_state()          # float-rounded input state
+        lat.step(1)
+        f, g = lat.get_state()
+    (fo, go), _ = _oracle_run(dims, p, to_oracle(fin), to_oracle(gin), 1)
+    _, w = oracle.velocity_set()
+    df = to_oracle(f) - fo
+    shift = fo - w[:, None] * p["rho0"]
+    assert np.abs(df).max() <= 4e-7 * np.abs(shift).max() + 1e-9
+    assert rel(to_oracle(g), go) <= 1e-6
