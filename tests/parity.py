@@ -14,12 +14,28 @@ P0 = dict(L.DEFAULT_PARAMS)
 TOL_FP64 = 1e-12
 
 
-def rel(a, b):
+def rel(a, b, scale=None):
     a = np.asarray(a, dtype=float)
     b = np.asarray(b, dtype=float)
-    scale = np.abs(b).max()
+    scale = np.abs(b).max() if scale is None else max(scale, np.abs(b).max())
     d = np.abs(a - b).max()
     return d / scale if scale > 0 else d
+
+
+def u_scale(f):
+    """Size of the terms whose sum gives u = sum_i f_i c_i / rho: the max over
+    sites and components of sum_i |f_i c_ia| / rho (oracle-order state).
+
+    Any floating-point evaluation of the sum carries an absolute error of
+    about eps times this, so u's error is measured against it: early in a
+    spinodal or interface run |u| is ~1e-8 while the summands are ~0.1, and
+    a scale of max|u| alone would ask for more digits than the data hold.
+    """
+    c, _ = oracle.velocity_set()
+    f = np.asarray(f, dtype=float)
+    rho = f.sum(0)
+    s = np.abs(f).T @ np.abs(c).astype(float)          # [N, 3]
+    return float((s / rho[:, None]).max())
 
 
 def abi_order():
