@@ -331,8 +331,11 @@ def run_step_only(args):
     lbpkg.build()
     dims = (args.lattice,) * 3
     params = dict(LI.DEFAULT_PARAMS)
+    cfg = tuning.bench_config(dims, args.precision)
+    if args.kernel:
+        cfg = (args.kernel, *args.block)
     with Lattice.from_params(dims, params, precision=args.precision) as lat:
-        lat.set_kernel(*tuning.bench_config(dims, args.precision))
+        lat.set_kernel(*cfg)
         lat.init(LI.spinodal_phi0(*dims, seed=1))
         lat.step(args.warmup)
         torch.cuda.synchronize()
@@ -340,7 +343,7 @@ def run_step_only(args):
         lat.step(args.steps)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-    print(json.dumps({"only": "step", "lattice": list(dims), "precision": args.precision,
+    print(json.dumps({"only": "step", "lattice": list(dims), "precision": args.precision, "launch": list(cfg),
                       "steps": args.steps, "MLUPS": math.prod(dims) * args.steps / dt / 1e6}))
 
 
@@ -354,6 +357,9 @@ def main():
                     help="run only timesteps of one lattice (profiling case)")
     ap.add_argument("--lattice", type=int, default=128, help="edge of the --only lattice")
     ap.add_argument("--precision", choices=["fp32_shifted", "fp64"], default="fp32_shifted")
+    ap.add_argument("--kernel", choices=["two_pass", "fused", "staged"], default=None,
+                    help="override the tuned launch of the --only lattice")
+    ap.add_argument("--block", type=int, nargs=3, default=(0, 0, 0), metavar=("BX", "BY", "ZC"))
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

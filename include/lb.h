@@ -74,7 +74,9 @@ enum { LB_HOST = 0, LB_DEVICE = 1 };
 enum {
     LB_KERNEL_AUTO = 0,     /* library default (the fused kernel)              */
     LB_KERNEL_TWO_PASS = 1, /* phi pass + collide/stream pass (phi buffer)     */
-    LB_KERNEL_FUSED = 2     /* single pass, phi halo staged in shared memory   */
+    LB_KERNEL_FUSED = 2,    /* single pass, phi halo staged in shared memory   */
+    LB_KERNEL_STAGED = 3    /* single pass, planes staged by asynchronous
+                               copies into a 3-buffer shared-memory pipeline   */
 };
 
 typedef struct lb_ctx lb_ctx;
@@ -165,7 +167,7 @@ int lb_set_state(lb_ctx *c, const double *f, const double *g, int ptr_kind);
 
 /* Select the step kernel (LB_KERNEL_*) and its launch shape: block_x x
  * block_y threads per CTA and z_chunk planes marched per CTA by the fused
- * kernel (0 = library default for any of the three).  Validated against the
+ * and staged kernels (0 = library default for any of the three).  Validated against the
  * kernel's limits; LB_ERR_INVALID otherwise.  Paper: the tunable VVL and TPB
  * of TARGET_TLP / TARGET_LAUNCH, Sec. III.C. */
 int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk);

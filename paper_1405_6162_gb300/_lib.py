@@ -28,6 +28,7 @@ LB_DEVICE = 1
 LB_KERNEL_AUTO = 0
 LB_KERNEL_TWO_PASS = 1
 LB_KERNEL_FUSED = 2
+LB_KERNEL_STAGED = 3
 
 
 class lb_params(ctypes.Structure):

@@ -11,9 +11,23 @@
 
 #include <cuda_runtime.h>
 
+#ifndef LBK_ST_CS
+#define LBK_ST_CS 0   // 1: stores of post-collision values with the streaming (.cs) hint
+#endif
+
 namespace lbk {
 
 constexpr int Q = 19;
+
+template <typename T>
+__device__ __forceinline__ void store(T *p, T v)
+{
+#if LBK_ST_CS
+    __stcs(p, v);
+#else
+    *p = v;
+#endif
+}
 
 // ABI velocity order: 0 rest; 1..6 faces; 7..18 edges; odd/even = opposite.
 __host__ __device__ constexpr int cx(int i) {

@@ -44,7 +44,7 @@ void dev_free(lb_ctx *c, void *p, size_t bytes)
         cudaFree(p);
 }
 
-size_t dist_bytes(const lb_ctx *c) { return (size_t)lbk::Q * (size_t)c->N * c->esize; }
+size_t dist_bytes(const lb_ctx *c) { return (size_t)lbk::Q * (size_t)c->S * c->esize; }
 size_t io_bytes(const lb_ctx *c) { return 5 * (size_t)c->N * sizeof(double); }
 
 void free_all(lb_ctx *c)
@@ -148,6 +148,7 @@ int lb_create(const lb_params *p, void *cuda_stream, lb_ctx **out)
     c->p = *p;
     c->stream = (cudaStream_t)cuda_stream;
     c->N = (long long)p->nx * p->ny * p->nz;
+    c->S = lbk::component_stride(c->N);
     c->esize = p->precision == LB_FP64 ? sizeof(double) : sizeof(float);
     {
         std::lock_guard<std::mutex> lk(g_alloc_mu);
@@ -224,16 +225,21 @@ int lb_step(lb_ctx *c, int nsteps)
     if (!c || nsteps < 0) return LB_ERR_INVALID;
     if (nsteps == 0) return LB_OK;
     if (c->kernel == LB_KERNEL_TWO_PASS) return lbk::launch_step_two_pass(c, nsteps);
+    if (c->kernel == LB_KERNEL_STAGED) return lbk::launch_step_staged(c, nsteps);
     return lbk::launch_step_fused(c, nsteps);
 }
 
 int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk)
 {
     if (!c) return LB_ERR_INVALID;
-    if (kernel != LB_KERNEL_AUTO && kernel != LB_KERNEL_TWO_PASS && kernel != LB_KERNEL_FUSED)
+    if (kernel != LB_KERNEL_AUTO && kernel != LB_KERNEL_TWO_PASS && kernel != LB_KERNEL_FUSED &&
+        kernel != LB_KERNEL_STAGED)
         return LB_ERR_INVALID;
     if (block_x < 0 || block_y < 0 || z_chunk < 0) return LB_ERR_INVALID;
-    if (kernel != LB_KERNEL_TWO_PASS) {
+    if (kernel == LB_KERNEL_STAGED) {
+        int rc = lbk::staged_validate(c->p.precision, block_x, block_y, z_chunk);
+        if (rc) return rc;
+    } else if (kernel != LB_KERNEL_TWO_PASS) {
         int rc = lbk::fused_validate(c->p.precision, block_x, block_y, z_chunk);
         if (rc) return rc;
     }

@@ -30,6 +30,7 @@ struct Geo {
     int bx, by, zc;      // tile extents and z-chunk length
     int tiles_x;         // tiles along x
     long long N;
+    long long S;         // component stride
 };
 
 template <typename T>
@@ -60,7 +61,7 @@ __device__ __forceinline__ T pulled_phi(const T *__restrict__ ga, const Geo &G, 
     T g[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++)
-        g[i] = ga[(size_t)i * G.N + (X[1 - cx(i)] + Y[1 - cy(i)] + Z[1 - cz(i)])];
+        g[i] = ga[(size_t)i * G.S + (X[1 - cx(i)] + Y[1 - cy(i)] + Z[1 - cz(i)])];
     return sum19(g);
 }
 
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxThreads64 : kMaxThreads) 
             T f[Q], g[Q];
 #pragma unroll
             for (int i = 0; i < Q; i++) {
-                const size_t o = (size_t)i * G.N + (X[1 - cx(i)] + Y[1 - cy(i)] + Z[1 - cz(i)]);
+                const size_t o = (size_t)i * G.S + (X[1 - cx(i)] + Y[1 - cy(i)] + Z[1 - cz(i)]);
                 f[i] = fa[o];
                 g[i] = ga[o];
             }
@@ -139,8 +140,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxThreads64 : kMaxThreads) 
             const size_t s = (size_t)(X[1] + Y[1] + Z[1]);
 #pragma unroll
             for (int i = 0; i < Q; i++) {
-                fb[(size_t)i * G.N + s] = f[i];
-                gb[(size_t)i * G.N + s] = g[i];
+                store(fb + (size_t)i * G.S + s, f[i]);
+                store(gb + (size_t)i * G.S + s, g[i]);
             }
         }
         __syncthreads();
@@ -162,6 +163,7 @@ int run(lb_ctx *c, int nsteps)
     G.ny = c->p.ny;
     G.nz = c->p.nz;
     G.N = c->N;
+    G.S = c->S;
     int bx = c->block_x, by = c->block_y, zc = c->z_chunk;
     defaults(c->p.precision, bx, by, zc);
     if ((G.nz + zc - 1) / zc > 65535) zc = (G.nz + 65534) / 65535;   // grid.y limit

@@ -7,7 +7,15 @@
 
 #include "lb.h"
 
+#ifndef LBK_COMPONENT_PAD
+#define LBK_COMPONENT_PAD 0
+#endif
+
 namespace lbk {
+
+// Component stride of the SoA distribution arrays: N rounded up to 64
+// elements, plus LBK_COMPONENT_PAD elements.
+inline long long component_stride(long long N) { return ((N + 63) / 64) * 64 + LBK_COMPONENT_PAD; }
 
 struct Buffers {
     void *f[2] = {nullptr, nullptr};  // SoA [19][N] in storage type, two time levels
@@ -22,6 +30,7 @@ struct lb_ctx {
     cudaStream_t stream;
     int device;
     long long N;
+    long long S;           // elements between distribution components (>= N, padded)
     size_t esize;          // 8 (FP64) or 4 (FP32 shifted)
     lbk::Buffers buf;      // post-collision (pre-streaming) distributions
     void *phi = nullptr;   // [N] storage type: order parameter of the two-pass kernel
@@ -57,5 +66,9 @@ int launch_reduce(lb_ctx *c, double *dev_out5);
 // fused kernel (lb_fused.cu)
 int launch_step_fused(lb_ctx *c, int nsteps);
 int fused_validate(int precision, int block_x, int block_y, int z_chunk);
+
+// staged kernel (lb_staged.cu)
+int launch_step_staged(lb_ctx *c, int nsteps);
+int staged_validate(int precision, int block_x, int block_y, int z_chunk);
 
 }  // namespace lbk

@@ -70,7 +70,7 @@ template <typename T, bool SH>
 __global__ void __launch_bounds__(256) k_init(const double *__restrict__ phi0,
                                               const double *__restrict__ u0,
                                               T *__restrict__ fa, T *__restrict__ ga,
-                                              Coll<double> p, int nx, int ny, int nz)
+                                              Coll<double> p, int nx, int ny, int nz, long long S)
 {
     const long long N = (long long)nx * ny * nz;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256) k_init(const double *__restrict__ phi0,
     // A_i(x - c_i) = feq_i(x): the first pull then yields the equilibrium.
     equilibria<double, SH>(p, R, jx, jy, jz, ph, dx, dy, dz, lap,
                            [&](int i, double fe, double ge) {
-                               const size_t o = (size_t)i * N + n.src(i);
+                               const size_t o = (size_t)i * S + n.src(i);
                                fa[o] = T(fe);
                                ga[o] = T(ge);
                            });
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) k_init(const double *__restrict__ phi0,
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_phi_pull(const T *__restrict__ ga, T *__restrict__ phi,
-                                                  int nx, int ny, int nz)
+                                                  int nx, int ny, int nz, long long S)
 {
     const long long N = (long long)nx * ny * nz;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256) k_phi_pull(const T *__restrict__ ga, T *_
     const Nbr n(s, nx, ny, nz);
     T g[Q];
 #pragma unroll
-    for (int i = 0; i < Q; i++) g[i] = ga[(size_t)i * N + n.src(i)];
+    for (int i = 0; i < Q; i++) g[i] = ga[(size_t)i * S + n.src(i)];
     phi[s] = sum19(g);
 }
 
@@ -112,7 +112,7 @@ template <typename T, bool SH>
 __global__ void __launch_bounds__(256) k_collide_pull(const T *__restrict__ fa, const T *__restrict__ ga,
                                                       const T *__restrict__ phi,
                                                       T *__restrict__ fb, T *__restrict__ gb,
-                                                      Coll<T> p, int nx, int ny, int nz)
+                                                      Coll<T> p, int nx, int ny, int nz, long long S)
 {
     const long long N = (long long)nx * ny * nz;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) k_collide_pull(const T *__restrict__ fa, 
     T f[Q], g[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        const size_t o = (size_t)i * N + n.src(i);
+        const size_t o = (size_t)i * S + n.src(i);
         f[i] = fa[o];
         g[i] = ga[o];
     }
@@ -131,8 +131,8 @@ __global__ void __launch_bounds__(256) k_collide_pull(const T *__restrict__ fa, 
     collide<T, SH>(p, f, g, ph, dx, dy, dz, lap);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        fb[(size_t)i * N + s] = f[i];
-        gb[(size_t)i * N + s] = g[i];
+        fb[(size_t)i * S + s] = f[i];
+        gb[(size_t)i * S + s] = g[i];
     }
 }
 
@@ -142,7 +142,7 @@ template <typename T, bool SH>
 __global__ void __launch_bounds__(256) k_moments(const T *__restrict__ fa, const T *__restrict__ ga,
                                                  double *__restrict__ rho, double *__restrict__ u,
                                                  double *__restrict__ phi, double rho0,
-                                                 int nx, int ny, int nz)
+                                                 int nx, int ny, int nz, long long S)
 {
     const long long N = (long long)nx * ny * nz;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256) k_moments(const T *__restrict__ fa, const
     double f[Q], g[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        const size_t o = (size_t)i * N + n.src(i);
+        const size_t o = (size_t)i * S + n.src(i);
         f[i] = double(fa[o]);
         g[i] = double(ga[o]);
     }
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) k_moments(const T *__restrict__ fa, const
 template <typename T>
 __global__ void __launch_bounds__(256) k_get_state(const T *__restrict__ a, double *__restrict__ out,
                                                    int i0, int i1, double shift_rho0,
-                                                   int nx, int ny, int nz)
+                                                   int nx, int ny, int nz, long long S)
 {
     const long long N = (long long)nx * ny * nz;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) k_get_state(const T *__restrict__ a, doub
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         if (i < i0 || i >= i1) continue;
-        out[(size_t)(i - i0) * N + s] = double(a[(size_t)i * N + n.src(i)]) + weight(i) * shift_rho0;
+        out[(size_t)(i - i0) * N + s] = double(a[(size_t)i * S + n.src(i)]) + weight(i) * shift_rho0;
     }
 }
 
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256) k_get_state(const T *__restrict__ a, doub
 template <typename T>
 __global__ void __launch_bounds__(256) k_set_state(T *__restrict__ a, const double *__restrict__ in,
                                                    int i0, int i1, double shift_rho0,
-                                                   int nx, int ny, int nz)
+                                                   int nx, int ny, int nz, long long S)
 {
     const long long N = (long long)nx * ny * nz;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(256) k_set_state(T *__restrict__ a, const doub
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         if (i < i0 || i >= i1) continue;
-        a[(size_t)i * N + n.src(i)] = T(in[(size_t)(i - i0) * N + s] - weight(i) * shift_rho0);
+        a[(size_t)i * S + n.src(i)] = T(in[(size_t)(i - i0) * N + s] - weight(i) * shift_rho0);
     }
 }
 
@@ -236,7 +236,8 @@ __device__ __forceinline__ void block_sum(double (&acc)[K], double *out)
 template <typename T>
 __global__ void __launch_bounds__(kReduceThreads) k_reduce_partial(const T *__restrict__ fa,
                                                                    const T *__restrict__ ga,
-                                                                   long long N, double *__restrict__ partial)
+                                                                   long long N, long long S,
+                                                                   double *__restrict__ partial)
 {
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < N;
@@ -244,8 +245,8 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_partial(const T *__re
         double f[Q], g[Q];
 #pragma unroll
         for (int i = 0; i < Q; i++) {
-            f[i] = double(fa[(size_t)i * N + s]);
-            g[i] = double(ga[(size_t)i * N + s]);
+            f[i] = double(fa[(size_t)i * S + s]);
+            g[i] = double(ga[(size_t)i * S + s]);
         }
         double R, jx, jy, jz;
         density_moments(f, R, jx, jy, jz);
@@ -286,10 +287,10 @@ int launch_init(lb_ctx *c, const double *phi0_d, const double *u0_d)
     const unsigned grid = grid_for(c->N, 256);
     if (c->p.precision == LB_FP64)
         k_init<double, false><<<grid, 256, 0, c->stream>>>(phi0_d, u0_d, (double *)c->buf.f[cur],
-                                                           (double *)c->buf.g[cur], p, c->p.nx, c->p.ny, c->p.nz);
+                                                           (double *)c->buf.g[cur], p, c->p.nx, c->p.ny, c->p.nz, c->S);
     else
         k_init<float, true><<<grid, 256, 0, c->stream>>>(phi0_d, u0_d, (float *)c->buf.f[cur],
-                                                         (float *)c->buf.g[cur], p, c->p.nx, c->p.ny, c->p.nz);
+                                                         (float *)c->buf.g[cur], p, c->p.nx, c->p.ny, c->p.nz, c->S);
     return check_launch();
 }
 
@@ -301,10 +302,10 @@ static int two_pass(lb_ctx *c, int nsteps)
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
     for (int t = 0; t < nsteps; t++) {
         const int a = c->buf.cur, b = 1 - a;
-        k_phi_pull<T><<<grid, 256, 0, c->stream>>>((const T *)c->buf.g[a], (T *)c->phi, nx, ny, nz);
+        k_phi_pull<T><<<grid, 256, 0, c->stream>>>((const T *)c->buf.g[a], (T *)c->phi, nx, ny, nz, c->S);
         k_collide_pull<T, SH><<<grid, 256, 0, c->stream>>>((const T *)c->buf.f[a], (const T *)c->buf.g[a],
                                                            (const T *)c->phi, (T *)c->buf.f[b],
-                                                           (T *)c->buf.g[b], p, nx, ny, nz);
+                                                           (T *)c->buf.g[b], p, nx, ny, nz, c->S);
         int rc = check_launch();
         if (rc) return rc;
         c->buf.cur = b;
@@ -324,11 +325,11 @@ int launch_moments(lb_ctx *c, double *rho, double *u, double *phi)
     if (c->p.precision == LB_FP64)
         k_moments<double, false><<<grid, 256, 0, c->stream>>>((const double *)c->buf.f[cur],
                                                               (const double *)c->buf.g[cur], rho, u, phi,
-                                                              c->p.rho0, c->p.nx, c->p.ny, c->p.nz);
+                                                              c->p.rho0, c->p.nx, c->p.ny, c->p.nz, c->S);
     else
         k_moments<float, true><<<grid, 256, 0, c->stream>>>((const float *)c->buf.f[cur],
                                                             (const float *)c->buf.g[cur], rho, u, phi,
-                                                            c->p.rho0, c->p.nx, c->p.ny, c->p.nz);
+                                                            c->p.rho0, c->p.nx, c->p.ny, c->p.nz, c->S);
     return check_launch();
 }
 
@@ -341,10 +342,10 @@ static int get_rows(lb_ctx *c, int which, int i0, int i1, double *out)
     void *a = which == 0 ? c->buf.f[cur] : c->buf.g[cur];
     if (c->p.precision == LB_FP64)
         k_get_state<double><<<grid, 256, 0, c->stream>>>((const double *)a, out, i0, i1, shift,
-                                                         c->p.nx, c->p.ny, c->p.nz);
+                                                         c->p.nx, c->p.ny, c->p.nz, c->S);
     else
         k_get_state<float><<<grid, 256, 0, c->stream>>>((const float *)a, out, i0, i1, shift,
-                                                        c->p.nx, c->p.ny, c->p.nz);
+                                                        c->p.nx, c->p.ny, c->p.nz, c->S);
     return check_launch();
 }
 
@@ -356,10 +357,10 @@ static int set_rows(lb_ctx *c, int which, int i0, int i1, const double *in)
     void *a = which == 0 ? c->buf.f[cur] : c->buf.g[cur];
     if (c->p.precision == LB_FP64)
         k_set_state<double><<<grid, 256, 0, c->stream>>>((double *)a, in, i0, i1, shift,
-                                                         c->p.nx, c->p.ny, c->p.nz);
+                                                         c->p.nx, c->p.ny, c->p.nz, c->S);
     else
         k_set_state<float><<<grid, 256, 0, c->stream>>>((float *)a, in, i0, i1, shift,
-                                                        c->p.nx, c->p.ny, c->p.nz);
+                                                        c->p.nx, c->p.ny, c->p.nz, c->S);
     return check_launch();
 }
 
@@ -390,10 +391,10 @@ int launch_reduce(lb_ctx *c, double *dev_out5)
     const double off = c->p.precision == LB_FP32_SHIFTED ? double(c->N) * c->p.rho0 : 0.0;
     if (c->p.precision == LB_FP64)
         k_reduce_partial<double><<<kReduceBlocks, kReduceThreads, 0, c->stream>>>(
-            (const double *)c->buf.f[cur], (const double *)c->buf.g[cur], c->N, c->partial);
+            (const double *)c->buf.f[cur], (const double *)c->buf.g[cur], c->N, c->S, c->partial);
     else
         k_reduce_partial<float><<<kReduceBlocks, kReduceThreads, 0, c->stream>>>(
-            (const float *)c->buf.f[cur], (const float *)c->buf.g[cur], c->N, c->partial);
+            (const float *)c->buf.f[cur], (const float *)c->buf.g[cur], c->N, c->S, c->partial);
     int rc = check_launch();
     if (rc) return rc;
     k_reduce_final<<<1, kReduceThreads, 0, c->stream>>>(c->partial, kReduceBlocks, off, dev_out5);

@@ -51,17 +51,22 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link liblb.so; returns its path."""
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out_dir=None) -> str:
+    """Compile and link liblb.so; returns its path.
+
+    ``extra_flags`` / ``out_dir`` build a variant elsewhere (e.g. with a -D
+    tuning macro) without touching the default library."""
+    OUT = out_dir or OUT_DIR
+    lib_path = os.path.join(OUT, "liblb.so")
+    if not force and out_dir is None and not extra_flags and up_to_date():
         return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+    os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
     srcs = _sources()
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -69,18 +74,18 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         results = list(ex.map(compile_one, srcs))
-    with open(os.path.join(OUT_DIR, "ptxas.log"), "w") as fh:
+    with open(os.path.join(OUT, "ptxas.log"), "w") as fh:
         for obj, log in results:
             fh.write(f"== {os.path.basename(obj)}\n{log}\n")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib_path)
     if verbose:
-        print(open(os.path.join(OUT_DIR, "ptxas.log")).read())
-    return LIB
+        print(open(os.path.join(OUT, "ptxas.log")).read())
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -46,8 +46,16 @@ def _broadcast(line):
     return np.broadcast_to(line, (FULL[2] * FULL[1], FULL[0])).reshape(-1)
 
 
-# FP32-shifted vs the FP64 oracle over these step counts, max-norm scaled
-TOL_FP32_1D = {"rho": 1e-9, "u": 1e-7, "phi": 1e-5}
+# FP32-shifted vs the FP64 oracle, per step run.  At a (near-)steady
+# interface every step repeats the same float rounding of the collision, so
+# the local errors grow linearly with the steps (measured at a tanh
+# interface of amplitude 1: rho 1e-8, u 1e-8, phi 3e-8 per step);
+# u is scaled by its summands (u_scale), rho and phi by their max-norms.
+TOL_FP32_1D_PER_STEP = {"rho": 2.5e-8, "u": 2.5e-8, "phi": 1e-7}
+
+
+def _tol(precision, name, nsteps):
+    return TOL_FP64 if precision == "fp64" else TOL_FP32_1D_PER_STEP[name] * nsteps
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_shifted"])
@@ -61,13 +69,12 @@ def test_flat_interface_256cubed_equals_1d_oracle(precision, amplitude):
         lat.init(_broadcast(line))
         lat.step(nsteps)
         rho, u, phi = lat.moments()
-    for name, a, b in (("rho", rho, want[0]), ("phi", phi, want[2])):
-        e = rel(a.reshape(-1, FULL[0]), b[None, :])
-        tol = TOL_FP64 if precision == "fp64" else TOL_FP32_1D[name]
-        assert e <= tol, (name, e)
-    ux = u[0].reshape(-1, FULL[0])
-    e = rel(ux, want[1][0][None, :], us)
-    assert e <= (TOL_FP64 if precision == "fp64" else TOL_FP32_1D["u"]), ("u", e)
+    errs = {"rho": rel(rho.reshape(-1, FULL[0]), want[0][None, :]),
+            "u": rel(u[0].reshape(-1, FULL[0]), want[1][0][None, :], us),
+            "phi": rel(phi.reshape(-1, FULL[0]), want[2][None, :])}
+    print(f"flat interface a={amplitude} {precision} after {nsteps} steps:", errs)
+    for name, e in errs.items():
+        assert e <= _tol(precision, name, nsteps), (name, e)
     assert np.abs(u[1:]).max() <= 1e-15
 
 
@@ -82,8 +89,9 @@ def test_shear_wave_256cubed_equals_1d_oracle(precision, tau):
         lat.init(np.zeros(int(np.prod(FULL))), np.stack([_broadcast(u_line[a]) for a in range(3)]))
         lat.step(nsteps)
         rho, u, phi = lat.moments()
-    tol = TOL_FP64 if precision == "fp64" else TOL_FP32_1D["u"]
-    assert rel(u[1].reshape(-1, FULL[0]), want[1][1][None, :], us) <= tol
+    e = rel(u[1].reshape(-1, FULL[0]), want[1][1][None, :], us)
+    print(f"shear wave tau={tau} {precision} after {nsteps} steps: u err {e:.3e}")
+    assert e <= _tol(precision, "u", nsteps)
     assert np.abs(phi).max() == 0.0
 
 
