@@ -75,8 +75,10 @@ enum {
     LB_KERNEL_AUTO = 0,     /* library default (the fused kernel)              */
     LB_KERNEL_TWO_PASS = 1, /* phi pass + collide/stream pass (phi buffer)     */
     LB_KERNEL_FUSED = 2,    /* single pass, phi halo staged in shared memory   */
-    LB_KERNEL_STAGED = 3    /* single pass, planes staged by asynchronous
+    LB_KERNEL_STAGED = 3,   /* single pass, planes staged by asynchronous
                                copies into a 3-buffer shared-memory pipeline   */
+    LB_KERNEL_SLAB = 4      /* single pass, per z-slab: phi of the slab into
+                               shared memory, then a barrier-free collision    */
 };
 
 typedef struct lb_ctx lb_ctx;
@@ -166,8 +168,8 @@ int lb_get_state(lb_ctx *c, double *f, double *g, int ptr_kind);
 int lb_set_state(lb_ctx *c, const double *f, const double *g, int ptr_kind);
 
 /* Select the step kernel (LB_KERNEL_*) and its launch shape: block_x x
- * block_y threads per CTA and z_chunk planes marched per CTA by the fused
- * and staged kernels (0 = library default for any of the three).  Validated against the
+ * block_y threads per CTA and z_chunk planes per CTA of the fused, staged
+ * and slab kernels (0 = library default for any of the three).  Validated against the
  * kernel's limits; LB_ERR_INVALID otherwise.  Paper: the tunable VVL and TPB
  * of TARGET_TLP / TARGET_LAUNCH, Sec. III.C. */
 int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk);

@@ -29,6 +29,7 @@ LB_KERNEL_AUTO = 0
 LB_KERNEL_TWO_PASS = 1
 LB_KERNEL_FUSED = 2
 LB_KERNEL_STAGED = 3
+LB_KERNEL_SLAB = 4
 
 
 class lb_params(ctypes.Structure):

@@ -46,12 +46,18 @@ __host__ __device__ constexpr double weight(int i) {
     return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
 }
 
-// Relaxation and free-energy parameters in the arithmetic type T.
+// Relaxation and free-energy parameters in the arithmetic type T.  The
+// relaxation constants fold omega = 1/tau into the lattice weights so that
+// the step evaluates f* = (1 - omega) f + omega feq with one multiply-add
+// per direction (likewise g with omega_g); they are computed in double on
+// the host and rounded once.
 template <typename T>
 struct Coll {
     T omega, omega_g;      // 1/tau, 1/tau_g
     T rho0;                // shift of the FP32 form
     T gamma, A, B, kappa;
+    T cf, f0, f1, f2, f1h, f2h, f1t, f2t;   // 1-omega; omega*w_k; omega*w_k*9/2; omega*w_k*3
+    T cg, g0, g1, g2, g1h, g2h, g1t, g2t;   // the same with omega_g
 };
 
 // Equilibria of f and g at one site.  R is rho (SH = false) or rho - rho0
@@ -142,19 +148,95 @@ __device__ __forceinline__ T sum19(const T (&g)[Q])
          + ((g[16] + g[17]) + g[18]);
 }
 
-// In-place BGK collision of one site given phi and its stencil values.
+// In-place BGK collision of one site given phi and its stencil values:
+// f*_i = (1 - omega) f_i + omega feq_i with omega feq_i expanded per weight
+// class (rest, face, edge) and per opposite pair, sharing every partial sum.
 template <typename T, bool SH>
 __device__ __forceinline__ void collide(const Coll<T>& p, T (&f)[Q], T (&g)[Q],
                                         T phi, T dx, T dy, T dz, T lap)
 {
     T R, jx, jy, jz;
     density_moments(f, R, jx, jy, jz);
-    const T om = p.omega, omg = p.omega_g;
-    equilibria<T, SH>(p, R, jx, jy, jz, phi, dx, dy, dz, lap,
-                      [&](int i, T feq, T geq) {
-                          f[i] = f[i] + om * (feq - f[i]);
-                          g[i] = g[i] + omg * (geq - g[i]);
-                      });
+    const T third = T(1.0 / 3.0), h = T(4.5);
+    const T rho = SH ? p.rho0 + R : R;
+    const T rinv = T(1) / rho;
+    const T ux = jx * rinv, uy = jy * rinv, uz = jz * rinv;
+    const T phi2 = phi * phi;
+    const T mu = phi * (p.A + p.B * phi2) - p.kappa * lap;
+    const T pb = phi2 * (T(0.5) * p.A + T(0.75) * p.B * phi2)
+               - p.kappa * (phi * lap + T(0.5) * (dx * dx + dy * dy + dz * dz));
+    // S = P + rho u u
+    const T Sxx = pb + p.kappa * dx * dx + jx * ux;
+    const T Syy = pb + p.kappa * dy * dy + jy * uy;
+    const T Szz = pb + p.kappa * dz * dz + jz * uz;
+    const T Sxy = p.kappa * dx * dy + jx * uy;
+    const T Sxz = p.kappa * dx * dz + jx * uz;
+    const T Syz = p.kappa * dy * dz + jy * uz;
+    const T t3 = (Sxx + Syy + Szz) * third;
+
+    // ---- f: omega feq_i = omega w_i (R - 9/2 t3) + 9/2 omega w_i c_i c_i : S + 3 omega w_i c_i . j
+    const T cf = p.cf;
+    const T b = R - h * t3;
+    f[0] = cf * f[0] + p.f0 * b;
+    const T B1 = p.f1 * b, B2 = p.f2 * b;
+#define LBK_FACE(IP, IM, SAA, JA)                                  \
+    {                                                              \
+        const T s_ = p.f1h * SAA + B1, a_ = p.f1t * JA;            \
+        f[IP] = cf * f[IP] + (s_ + a_);                            \
+        f[IM] = cf * f[IM] + (s_ - a_);                            \
+    }
+    LBK_FACE(1, 2, Sxx, jx)
+    LBK_FACE(3, 4, Syy, jy)
+    LBK_FACE(5, 6, Szz, jz)
+#undef LBK_FACE
+    // edge pairs (a+b, -a-b) = (IP, IM) and (a-b, -a+b) = (KP, KM); 2 f2h = f1h
+#define LBK_EDGES(IP, IM, KP, KM, SAA, SBB, SAB, JA, JB)             \
+    {                                                                \
+        const T e_ = p.f2h * (SAA + SBB) + B2, o_ = p.f1h * SAB;     \
+        const T sp = e_ + o_, sm = e_ - o_;                          \
+        const T ap = p.f2t * (JA + JB), am = p.f2t * (JA - JB);      \
+        f[IP] = cf * f[IP] + (sp + ap);                              \
+        f[IM] = cf * f[IM] + (sp - ap);                              \
+        f[KP] = cf * f[KP] + (sm + am);                              \
+        f[KM] = cf * f[KM] + (sm - am);                              \
+    }
+    LBK_EDGES(7, 8, 9, 10, Sxx, Syy, Sxy, jx, jy)
+    LBK_EDGES(11, 12, 13, 14, Sxx, Szz, Sxz, jx, jz)
+    LBK_EDGES(15, 16, 17, 18, Syy, Szz, Syz, jy, jz)
+#undef LBK_EDGES
+
+    // ---- g: omega_g geq_i = omega_g w_i [phi + 3 phi c.u + 9/2 (phi (c.u)^2 - phi u^2/3 + (Gamma mu - phi/3)(c^2 - 1))]
+    const T cg = p.cg;
+    const T px = phi * ux, py = phi * uy, pz = phi * uz;
+    const T pu2 = (px * ux + py * uy + pz * uz) * third;
+    const T gm = p.gamma * mu - phi * third;
+    const T bg = phi - h * pu2;
+    g[0] = cg * g[0] + p.g0 * (bg - h * gm);
+    const T G1 = p.g1 * bg, G2 = p.g2 * (bg + h * gm);
+#define LBK_GFACE(IP, IM, PA, UA)                                   \
+    {                                                               \
+        const T s_ = p.g1h * (PA * UA) + G1, a_ = p.g1t * PA;       \
+        g[IP] = cg * g[IP] + (s_ + a_);                             \
+        g[IM] = cg * g[IM] + (s_ - a_);                             \
+    }
+    LBK_GFACE(1, 2, px, ux)
+    LBK_GFACE(3, 4, py, uy)
+    LBK_GFACE(5, 6, pz, uz)
+#undef LBK_GFACE
+#define LBK_GEDGE(IP, IM, PC, CU)                                   \
+    {                                                               \
+        const T pc_ = PC, cu_ = CU;                                 \
+        const T s_ = p.g2h * (pc_ * cu_) + G2, a_ = p.g2t * pc_;    \
+        g[IP] = cg * g[IP] + (s_ + a_);                             \
+        g[IM] = cg * g[IM] + (s_ - a_);                             \
+    }
+    LBK_GEDGE(7, 8, px + py, ux + uy)
+    LBK_GEDGE(9, 10, px - py, ux - uy)
+    LBK_GEDGE(11, 12, px + pz, ux + uz)
+    LBK_GEDGE(13, 14, px - pz, ux - uz)
+    LBK_GEDGE(15, 16, py + pz, uy + uz)
+    LBK_GEDGE(17, 18, py - pz, uy - uz)
+#undef LBK_GEDGE
 }
 
 }  // namespace lbk

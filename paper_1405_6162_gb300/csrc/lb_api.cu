@@ -226,18 +226,20 @@ int lb_step(lb_ctx *c, int nsteps)
     if (nsteps == 0) return LB_OK;
     if (c->kernel == LB_KERNEL_TWO_PASS) return lbk::launch_step_two_pass(c, nsteps);
     if (c->kernel == LB_KERNEL_STAGED) return lbk::launch_step_staged(c, nsteps);
+    if (c->kernel == LB_KERNEL_SLAB) return lbk::launch_step_slab(c, nsteps);
     return lbk::launch_step_fused(c, nsteps);
 }
 
 int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk)
 {
     if (!c) return LB_ERR_INVALID;
-    if (kernel != LB_KERNEL_AUTO && kernel != LB_KERNEL_TWO_PASS && kernel != LB_KERNEL_FUSED &&
-        kernel != LB_KERNEL_STAGED)
-        return LB_ERR_INVALID;
+    if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_SLAB) return LB_ERR_INVALID;
     if (block_x < 0 || block_y < 0 || z_chunk < 0) return LB_ERR_INVALID;
     if (kernel == LB_KERNEL_STAGED) {
         int rc = lbk::staged_validate(c->p.precision, block_x, block_y, z_chunk);
+        if (rc) return rc;
+    } else if (kernel == LB_KERNEL_SLAB) {
+        int rc = lbk::slab_validate(c->p.precision, block_x, block_y, z_chunk);
         if (rc) return rc;
     } else if (kernel != LB_KERNEL_TWO_PASS) {
         int rc = lbk::fused_validate(c->p.precision, block_x, block_y, z_chunk);

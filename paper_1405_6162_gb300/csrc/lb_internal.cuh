@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include "d3q19.cuh"
 #include "lb.h"
 
 #ifndef LBK_COMPONENT_PAD
@@ -49,6 +50,31 @@ namespace lbk {
 constexpr int kReduceBlocks = 608;   // 4 x 152 SMs; fixed so sums are reproducible
 constexpr int kReduceThreads = 256;
 
+// Parameters of the step in the arithmetic type T (constants formed in
+// double, rounded once).
+template <typename T>
+inline Coll<T> make_coll(const lb_params &p)
+{
+    const double om = 1.0 / p.tau, og = 1.0 / p.tau_g;
+    Coll<T> c;
+    c.omega = T(om);
+    c.omega_g = T(og);
+    c.rho0 = T(p.rho0);
+    c.gamma = T(p.gamma);
+    c.A = T(p.A);
+    c.B = T(p.B);
+    c.kappa = T(p.kappa);
+    c.cf = T(1.0 - om);
+    c.f0 = T(om / 3.0);  c.f1 = T(om / 18.0);  c.f2 = T(om / 36.0);
+    c.f1h = T(om / 4.0); c.f2h = T(om / 8.0);
+    c.f1t = T(om / 6.0); c.f2t = T(om / 12.0);
+    c.cg = T(1.0 - og);
+    c.g0 = T(og / 3.0);  c.g1 = T(og / 18.0);  c.g2 = T(og / 36.0);
+    c.g1h = T(og / 4.0); c.g2h = T(og / 8.0);
+    c.g1t = T(og / 6.0); c.g2t = T(og / 12.0);
+    return c;
+}
+
 // status helpers (lb_api.cu)
 int cuda_status(cudaError_t e);
 int check_launch();
@@ -70,5 +96,9 @@ int fused_validate(int precision, int block_x, int block_y, int z_chunk);
 // staged kernel (lb_staged.cu)
 int launch_step_staged(lb_ctx *c, int nsteps);
 int staged_validate(int precision, int block_x, int block_y, int z_chunk);
+
+// slab kernel (lb_slab.cu)
+int launch_step_slab(lb_ctx *c, int nsteps);
+int slab_validate(int precision, int block_x, int block_y, int z_chunk);
 
 }  // namespace lbk

@@ -38,20 +38,6 @@ struct Nbr {
 };
 
 template <typename T>
-Coll<T> make_coll(const lb_params &p)
-{
-    Coll<T> c;
-    c.omega = T(1.0 / p.tau);
-    c.omega_g = T(1.0 / p.tau_g);
-    c.rho0 = T(p.rho0);
-    c.gamma = T(p.gamma);
-    c.A = T(p.A);
-    c.B = T(p.B);
-    c.kappa = T(p.kappa);
-    return c;
-}
-
-template <typename T>
 __device__ __forceinline__ void stencil(const T *__restrict__ phi, const Nbr &n, T ph,
                                         T &dx, T &dy, T &dz, T &lap)
 {

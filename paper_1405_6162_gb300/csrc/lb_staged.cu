@@ -27,20 +27,6 @@ struct SGeo {
     long long S;         // component stride
 };
 
-template <typename T>
-Coll<T> coll_of(const lb_params &p)
-{
-    Coll<T> c;
-    c.omega = T(1.0 / p.tau);
-    c.omega_g = T(1.0 / p.tau_g);
-    c.rho0 = T(p.rho0);
-    c.gamma = T(p.gamma);
-    c.A = T(p.A);
-    c.B = T(p.B);
-    c.kappa = T(p.kappa);
-    return c;
-}
-
 __device__ __forceinline__ int wrap_lo(int v, int n) { return v < 0 ? v + n : v; }
 __device__ __forceinline__ int wrap_hi(int v, int n) { return v >= n ? v - n : v; }
 
@@ -252,7 +238,7 @@ int run_staged(lb_ctx *c, int nsteps)
     const size_t shm = smem_bytes<T>(bx, by);
     int rc = cuda_status(cudaFuncSetAttribute(k_staged<T, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     if (rc) return rc;
-    const auto p = coll_of<T>(c->p);
+    const auto p = make_coll<T>(c->p);
     for (int t = 0; t < nsteps; t++) {
         const int a = c->buf.cur, b = 1 - a;
         k_staged<T, SH><<<grid, block, shm, c->stream>>>((const T *)c->buf.f[a], (const T *)c->buf.g[a],

@@ -18,7 +18,8 @@ pytestmark = pytest.mark.gpu
 # every kernel, default and ragged-forcing launch shapes (valid in FP64 too)
 KERNEL_CASES = [("two_pass", (0, 0, 0)), ("fused", (0, 0, 0)), ("fused", (64, 2, 5)),
                 ("fused", (32, 1, 1)), ("fused", (128, 2, 7)), ("staged", (0, 0, 0)),
-                ("staged", (64, 2, 5)), ("staged", (32, 1, 1)), ("staged", (32, 4, 3))]
+                ("staged", (64, 2, 5)), ("staged", (32, 1, 1)), ("staged", (32, 4, 3)),
+                ("slab", (0, 0, 0)), ("slab", (64, 2, 5)), ("slab", (32, 1, 1)), ("slab", (128, 2, 3))]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -85,7 +86,8 @@ def test_fused_and_two_pass_bitwise_identical(precision):
     f0, g0 = nonequilibrium_state(dims, p, seed=41)
     out = []
     for kernel, block in (("two_pass", (0, 0, 0)), ("fused", (32, 4, 6)), ("fused", (64, 4, 32)),
-                          ("staged", (32, 4, 6)), ("staged", (64, 2, 32))):
+                          ("staged", (32, 4, 6)), ("staged", (64, 2, 32)), ("slab", (32, 4, 6)),
+                          ("slab", (64, 4, 2))):
         with gpu_lattice(dims, p, precision, kernel, block) as lat:
             lat.set_state(to_abi(f0), to_abi(g0))
             lat.step(6)
@@ -173,7 +175,7 @@ def test_nonfinite_state_is_reported():
 TOL_FP32 = {"rho": 1e-9, "u": 1e-7, "phi": 1e-5}
 
 
-@pytest.mark.parametrize("kernel,block", KERNEL_CASES[:3] + KERNEL_CASES[5:7])
+@pytest.mark.parametrize("kernel,block", KERNEL_CASES[:3] + KERNEL_CASES[5:7] + KERNEL_CASES[9:11])
 def test_spinodal_32cubed_fp32_shifted(kernel, block):
     dims = (32, 32, 32)
     phi0 = L.spinodal_phi0(*dims, seed=0)
@@ -187,7 +189,7 @@ def test_spinodal_32cubed_fp32_shifted(kernel, block):
     _check_moments(got, mo, TOL_FP32, fo)
 
 
-@pytest.mark.parametrize("kernel", ["fused", "staged"])
+@pytest.mark.parametrize("kernel", ["fused", "staged", "slab"])
 @pytest.mark.parametrize("dims", [(13, 7, 5), (40, 9, 35), (1, 1, 3)])
 def test_ragged_fp32_shifted_one_step(dims, kernel):
     """One step from a float-representable state: the only difference from
