@@ -22,7 +22,13 @@ namespace lbk {
 
 namespace {
 
-constexpr int kMaxThreads = 512;      // FP32 CTA size limit
+#ifndef LBK_FUSED_MAXT32
+#define LBK_FUSED_MAXT32 512  // FP32 CTA size limit
+#endif
+#ifndef LBK_FUSED_MINB32
+#define LBK_FUSED_MINB32 1    // FP32 CTAs per SM the register budget must allow
+#endif
+constexpr int kMaxThreads = LBK_FUSED_MAXT32;
 constexpr int kMaxThreads64 = 256;    // FP64: more registers per thread
 
 struct Geo {
@@ -52,7 +58,8 @@ __device__ __forceinline__ T pulled_phi(const T *__restrict__ ga, const Geo &G, 
 }
 
 template <typename T, bool SH>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxThreads64 : kMaxThreads) k_fused(const T *__restrict__ fa, const T *__restrict__ ga,
+__global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxThreads64 : kMaxThreads,
+                                  sizeof(T) == 8 ? 1 : LBK_FUSED_MINB32) k_fused(const T *__restrict__ fa, const T *__restrict__ ga,
                                                        T *__restrict__ fb, T *__restrict__ gb,
                                                        Coll<T> p, Geo G)
 {

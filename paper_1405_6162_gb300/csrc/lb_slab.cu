@@ -19,7 +19,13 @@ namespace lbk {
 
 namespace {
 
-constexpr int kSlabMaxThreads = 512;
+#ifndef LBK_SLAB_MAXT32
+#define LBK_SLAB_MAXT32 512   // FP32 CTA size limit
+#endif
+#ifndef LBK_SLAB_MINB32
+#define LBK_SLAB_MINB32 1     // FP32 CTAs per SM the register budget must allow
+#endif
+constexpr int kSlabMaxThreads = LBK_SLAB_MAXT32;
 constexpr int kSlabMaxThreads64 = 256;
 
 struct BGeo {
@@ -46,7 +52,8 @@ __device__ __forceinline__ T pulled_phi(const T *__restrict__ ga, const BGeo &G,
 }
 
 template <typename T, bool SH>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? kSlabMaxThreads64 : kSlabMaxThreads)
+__global__ void __launch_bounds__(sizeof(T) == 8 ? kSlabMaxThreads64 : kSlabMaxThreads,
+                                  sizeof(T) == 8 ? 1 : LBK_SLAB_MINB32)
 k_slab(const T *__restrict__ fa, const T *__restrict__ ga, T *__restrict__ fb, T *__restrict__ gb,
        Coll<T> p, BGeo G)
 {
