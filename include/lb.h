@@ -77,8 +77,11 @@ enum {
     LB_KERNEL_FUSED = 2,    /* single pass, phi halo staged in shared memory   */
     LB_KERNEL_STAGED = 3,   /* single pass, planes staged by asynchronous
                                copies into a 3-buffer shared-memory pipeline   */
-    LB_KERNEL_SLAB = 4      /* single pass, per z-slab: phi of the slab into
+    LB_KERNEL_SLAB = 4,     /* single pass, per z-slab: phi of the slab into
                                shared memory, then a barrier-free collision    */
+    LB_KERNEL_LAG = 5       /* single pass, lagged pipeline: the CTA with
+                               ticket c computes phi of site block c and
+                               collides block c - D; bounded waits            */
 };
 
 typedef struct lb_ctx lb_ctx;
@@ -169,10 +172,32 @@ int lb_set_state(lb_ctx *c, const double *f, const double *g, int ptr_kind);
 
 /* Select the step kernel (LB_KERNEL_*) and its launch shape: block_x x
  * block_y threads per CTA and z_chunk planes per CTA of the fused, staged
- * and slab kernels (0 = library default for any of the three).  Validated against the
+ * and slab kernels (0 = library default for any of the three).  For
+ * LB_KERNEL_LAG block_x must be 0 or 256, block_y 0 or 1, and z_chunk is the
+ * lag slack in site blocks beyond the stencil's reach (0 = default 64).  Validated against the
  * kernel's limits; LB_ERR_INVALID otherwise.  Paper: the tunable VVL and TPB
  * of TARGET_TLP / TARGET_LAUNCH, Sec. III.C. */
 int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk);
+
+/* Synchronise the context's stream; returns LB_ERR_TIMEOUT if a bounded
+ * device-side wait (the lagged kernel's inter-CTA waits) gave up since the
+ * last synchronising call -- the state is then invalid until lb_init or
+ * lb_set_state -- else LB_OK or LB_ERR_CUDA.  Every call that synchronises
+ * (host-pointer lb_moments / lb_get_state / lb_set_state / lb_init,
+ * lb_reduce) reports such a timeout the same way.
+ * Paper: syncTarget (cudaThreadSynchronize with error checking), Sec. III.C. */
+int lb_sync(lb_ctx *c);
+
+/* Upper bound, in nanoseconds (1e3 .. 6e10), of every device-side wait of
+ * the context (default 1e9).  Paper: no counterpart (the paper's kernels
+ * never wait on one another). */
+int lb_set_wait_timeout(lb_ctx *c, long long timeout_ns);
+
+/* Test hook: add `skew` to the lagged kernel's wait targets so that no wait
+ * can be satisfied and every one runs into its time bound (the timeout path
+ * without a GPU fault).  0 restores normal operation.  Paper: no
+ * counterpart. */
+int lb_debug_wait_skew(lb_ctx *c, unsigned long long skew);
 
 /* Extents and precision of c (any output may be NULL). */
 int lb_get_info(const lb_ctx *c, int *nx, int *ny, int *nz, int *precision);

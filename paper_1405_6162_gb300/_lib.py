@@ -30,6 +30,7 @@ LB_KERNEL_TWO_PASS = 1
 LB_KERNEL_FUSED = 2
 LB_KERNEL_STAGED = 3
 LB_KERNEL_SLAB = 4
+LB_KERNEL_LAG = 5
 
 
 class lb_params(ctypes.Structure):
@@ -59,6 +60,9 @@ SIGNATURES = {
     "lb_set_state": (_I, [_P, _P, _P, _I]),
     "lb_set_kernel": (_I, [_P, _I, _I, _I, _I]),
     "lb_get_info": (_I, [_P, _P, _P, _P, _P]),
+    "lb_sync": (_I, [_P]),
+    "lb_set_wait_timeout": (_I, [_P, ctypes.c_longlong]),
+    "lb_debug_wait_skew": (_I, [_P, ctypes.c_ulonglong]),
     "lb_strerror": (ctypes.c_char_p, [_I]),
     "lb_last_error": (ctypes.c_char_p, []),
 }

@@ -58,6 +58,10 @@ void free_all(lb_ctx *c)
     dev_free(c, c->io, io_bytes(c));
     dev_free(c, c->partial, (size_t)lbk::kReduceBlocks * 5 * sizeof(double));
     dev_free(c, c->dev_out, 8 * sizeof(double));
+    dev_free(c, c->lag_counters, (size_t)(c->p.nz + 1) * sizeof(unsigned long long));
+    dev_free(c, c->err_flag, sizeof(unsigned int));
+    c->lag_counters = nullptr;
+    c->err_flag = nullptr;
     c->phi = nullptr;
     c->io = nullptr;
     c->partial = nullptr;
@@ -87,7 +91,21 @@ int ensure_io(lb_ctx *c)
     return c->io ? LB_OK : LB_ERR_NOMEM;
 }
 
-int sync(lb_ctx *c) { return lbk::cuda_status(cudaStreamSynchronize(c->stream)); }
+// Synchronise the stream, then report (and clear) a device-side wait that
+// gave up since the last check.
+int sync(lb_ctx *c)
+{
+    unsigned int flag = 0;
+    int rc = lbk::cuda_status(cudaMemcpyAsync(&flag, c->err_flag, sizeof(flag), cudaMemcpyDeviceToHost, c->stream));
+    if (!rc) rc = lbk::cuda_status(cudaStreamSynchronize(c->stream));
+    if (rc) return rc;
+    if (flag) {
+        rc = lbk::cuda_status(cudaMemsetAsync(c->err_flag, 0, sizeof(unsigned int), c->stream));
+        if (!rc) rc = lbk::cuda_status(cudaStreamSynchronize(c->stream));
+        return rc ? rc : LB_ERR_TIMEOUT;
+    }
+    return LB_OK;
+}
 
 int copy(lb_ctx *c, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind)
 {
@@ -168,13 +186,18 @@ int lb_create(const lb_params *p, void *cuda_stream, lb_ctx **out)
     c->phi = dev_alloc(c, (size_t)c->N * c->esize);
     c->partial = (double *)dev_alloc(c, (size_t)lbk::kReduceBlocks * 5 * sizeof(double));
     c->dev_out = (double *)dev_alloc(c, 8 * sizeof(double));
-    bool ok = c->phi && c->partial && c->dev_out;
+    c->lag_counters = (unsigned long long *)dev_alloc(c, (size_t)(p->nz + 1) * sizeof(unsigned long long));
+    c->err_flag = (unsigned int *)dev_alloc(c, sizeof(unsigned int));
+    bool ok = c->phi && c->partial && c->dev_out && c->lag_counters && c->err_flag;
     for (int k = 0; k < 2; k++) ok = ok && c->buf.f[k] && c->buf.g[k];
     if (!ok) {
         free_all(c);
         delete c;
         return LB_ERR_NOMEM;
     }
+    rc = lbk::cuda_status(cudaMemsetAsync(c->lag_counters, 0, (size_t)(p->nz + 1) * sizeof(unsigned long long),
+                                          c->stream));
+    if (!rc) rc = lbk::cuda_status(cudaMemsetAsync(c->err_flag, 0, sizeof(unsigned int), c->stream));
     for (int k = 0; k < 2 && !rc; k++) {
         rc = lbk::cuda_status(cudaMemsetAsync(c->buf.f[k], 0, dist_bytes(c), c->stream));
         if (!rc) rc = lbk::cuda_status(cudaMemsetAsync(c->buf.g[k], 0, dist_bytes(c), c->stream));
@@ -194,6 +217,26 @@ void lb_destroy(lb_ctx *c)
     cudaGetLastError();
     free_all(c);
     delete c;
+}
+
+int lb_sync(lb_ctx *c)
+{
+    if (!c) return LB_ERR_INVALID;
+    return sync(c);
+}
+
+int lb_set_wait_timeout(lb_ctx *c, long long timeout_ns)
+{
+    if (!c || timeout_ns < 1000 || timeout_ns > 60000000000LL) return LB_ERR_INVALID;
+    c->wait_timeout_ns = timeout_ns;
+    return LB_OK;
+}
+
+int lb_debug_wait_skew(lb_ctx *c, unsigned long long skew)
+{
+    if (!c) return LB_ERR_INVALID;
+    c->lag_target_skew = skew;
+    return LB_OK;
 }
 
 int lb_get_info(const lb_ctx *c, int *nx, int *ny, int *nz, int *precision)
@@ -227,16 +270,20 @@ int lb_step(lb_ctx *c, int nsteps)
     if (c->kernel == LB_KERNEL_TWO_PASS) return lbk::launch_step_two_pass(c, nsteps);
     if (c->kernel == LB_KERNEL_STAGED) return lbk::launch_step_staged(c, nsteps);
     if (c->kernel == LB_KERNEL_SLAB) return lbk::launch_step_slab(c, nsteps);
+    if (c->kernel == LB_KERNEL_LAG) return lbk::launch_step_lag(c, nsteps);
     return lbk::launch_step_fused(c, nsteps);
 }
 
 int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk)
 {
     if (!c) return LB_ERR_INVALID;
-    if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_SLAB) return LB_ERR_INVALID;
+    if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_LAG) return LB_ERR_INVALID;
     if (block_x < 0 || block_y < 0 || z_chunk < 0) return LB_ERR_INVALID;
     if (kernel == LB_KERNEL_STAGED) {
         int rc = lbk::staged_validate(c->p.precision, block_x, block_y, z_chunk);
+        if (rc) return rc;
+    } else if (kernel == LB_KERNEL_LAG) {
+        int rc = lbk::lag_validate(block_x, block_y, z_chunk);
         if (rc) return rc;
     } else if (kernel == LB_KERNEL_SLAB) {
         int rc = lbk::slab_validate(c->p.precision, block_x, block_y, z_chunk);

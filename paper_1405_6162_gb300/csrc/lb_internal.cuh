@@ -38,6 +38,11 @@ struct lb_ctx {
     double *io = nullptr;  // [4N] FP64 staging for host transfers (lazy)
     double *partial = nullptr;  // reduction partials [kReduceBlocks][5]
     double *dev_out = nullptr;  // [8] reduction result
+    // lagged kernel: [0] = CTA ticket counter, [1 + z] = phi-done counter of plane z
+    unsigned long long *lag_counters = nullptr;
+    unsigned int *err_flag = nullptr;         // set by a device-side wait that timed out
+    unsigned long long lag_target_skew = 0;   // test hook: makes the waits unsatisfiable
+    long long wait_timeout_ns = 1000000000LL; // bound of every device-side wait
     int kernel = LB_KERNEL_AUTO;
     int block_x = 0, block_y = 0, z_chunk = 0;
     lb_alloc_fn alloc = nullptr;
@@ -47,6 +52,8 @@ struct lb_ctx {
 
 namespace lbk {
 
+constexpr int kLagBlock = 256;       // sites per block of the lagged kernel
+constexpr long long kLagSlack = 64;   // extra lag (blocks) beyond the stencil reach
 constexpr int kReduceBlocks = 608;   // 4 x 152 SMs; fixed so sums are reproducible
 constexpr int kReduceThreads = 256;
 
@@ -96,6 +103,10 @@ int fused_validate(int precision, int block_x, int block_y, int z_chunk);
 // staged kernel (lb_staged.cu)
 int launch_step_staged(lb_ctx *c, int nsteps);
 int staged_validate(int precision, int block_x, int block_y, int z_chunk);
+
+// lagged kernel (lb_lag.cu)
+int launch_step_lag(lb_ctx *c, int nsteps);
+int lag_validate(int block_x, int block_y, int z_chunk);
 
 // slab kernel (lb_slab.cu)
 int launch_step_slab(lb_ctx *c, int nsteps);

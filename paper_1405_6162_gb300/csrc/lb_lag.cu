@@ -1,0 +1,223 @@
+// lb_lag.cu -- single-pass timestep with a lagged phi / collision pipeline.
+//
+// Sites are cut into blocks of kLagBlock consecutive indices (one CTA each).
+// The CTA holding ticket c (tickets are taken from a global counter when the
+// CTA starts, so a lower ticket always belongs to a CTA that has already
+// started) first computes phi = sum of the 19 pulled g values for block c and
+// stores it, then collides block c - D.  D exceeds the distance in blocks
+// between a site and its farthest stencil neighbour (one plane up), so every
+// phi a collision needs was produced by a CTA with a lower ticket; completion
+// is published per plane with a counter and awaited with a time-bounded spin
+// (on timeout the CTA records an error flag and returns).  Between the two
+// uses of a g value lie only about D blocks of traffic (~16 MB at 256^3), so
+// the collision's g reads hit L2: DRAM traffic stays near the 76 words per
+// site of the algorithm while every thread keeps the simple one-site,
+// barrier-free access pattern of a plain pull kernel.
+//
+// The lattice's first plane wraps onto the last, so blocks touching plane 0
+// are collided last (collision order b = (q + b0) mod nblocks).
+#include <cuda_runtime.h>
+
+#include "d3q19.cuh"
+#include "lb_internal.cuh"
+
+namespace lbk {
+
+namespace {
+
+struct LGeo {
+    int nx, ny, nz;
+    long long N, S;
+    long long plane;          // nx * ny
+    long long nblocks;        // ceil(N / kLagBlock)
+    long long D;              // lag in blocks
+    long long b0;             // blocks touching plane 0
+    unsigned long long ticket_base;
+    unsigned long long target;   // plane counter value meaning "done this launch"
+    long long timeout_ns;
+};
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long load_acquire(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+
+__device__ __forceinline__ void coords(long long s, const LGeo &G, int &x, int &y, int &z)
+{
+    const long long r = s / G.nx;
+    x = (int)(s - r * G.nx);
+    z = (int)(r / G.ny);
+    y = (int)(r - (long long)z * G.ny);
+}
+
+template <typename T, bool SH>
+__global__ void __launch_bounds__(kLagBlock) k_lag(const T *__restrict__ fa, const T *__restrict__ ga,
+                                                   T *__restrict__ fb, T *__restrict__ gb, T *phi,
+                                                   Coll<T> p, LGeo G, unsigned long long *ticket,
+                                                   unsigned long long *plane_done, unsigned int *err)
+{
+    __shared__ long long s_c;
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) {
+        s_c = (long long)(atomicAdd(ticket, 1ULL) - G.ticket_base);
+        s_fail = 0;
+    }
+    __syncthreads();
+    const long long c = s_c;
+
+    // ---- phase 1: phi of block c
+    if (c < G.nblocks) {
+        const long long s = c * kLagBlock + threadIdx.x;
+        if (s < G.N) {
+            int x, y, z;
+            coords(s, G, x, y, z);
+            const int X[3] = {x == 0 ? G.nx - 1 : x - 1, x, x + 1 == G.nx ? 0 : x + 1};
+            const long long Y[3] = {(long long)(y == 0 ? G.ny - 1 : y - 1) * G.nx, (long long)y * G.nx,
+                                    (long long)(y + 1 == G.ny ? 0 : y + 1) * G.nx};
+            const long long Z[3] = {(z == 0 ? G.nz - 1 : z - 1) * G.plane, z * G.plane,
+                                    (z + 1 == G.nz ? 0 : z + 1) * G.plane};
+            T g[Q];
+#pragma unroll
+            for (int i = 0; i < Q; i++) g[i] = ga[(size_t)i * G.S + (X[1 - cx(i)] + Y[1 - cy(i)] + Z[1 - cz(i)])];
+            phi[s] = sum19(g);
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const long long first = c * kLagBlock;
+            const long long last = min(first + kLagBlock, G.N) - 1;
+            for (long long pl = first / G.plane; pl <= last / G.plane; pl++) {
+                const long long lo = max(first, pl * G.plane), hi = min(last, (pl + 1) * G.plane - 1);
+                atomicAdd(plane_done + pl, (unsigned long long)(hi - lo + 1));
+            }
+        }
+    }
+
+    // ---- phase 2: collide block b = (c - D + b0) mod nblocks
+    const long long q = c - G.D;
+    if (q < 0) return;
+    long long b = q + G.b0;
+    if (b >= G.nblocks) b -= G.nblocks;
+    if (threadIdx.x == 0) {
+        const long long first = b * kLagBlock;
+        const long long last = min(first + kLagBlock, G.N) - 1;
+        const long long p0 = first / G.plane, p1 = last / G.plane;
+        const unsigned long long t0 = global_ns();
+        int fail = (*(volatile unsigned int *)err) != 0;   // an earlier CTA already gave up
+        for (long long k = p0 - 1; k <= p1 + 1 && k - (p0 - 1) < G.nz && !fail; k++) {
+            const long long pl = k < 0 ? k + G.nz : (k >= G.nz ? k - G.nz : k);
+            while (load_acquire(plane_done + pl) < G.target) {
+                if ((long long)(global_ns() - t0) > G.timeout_ns) {
+                    atomicOr(err, 1u);
+                    fail = 1;
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __threadfence();
+        s_fail = fail;
+    }
+    __syncthreads();
+    if (s_fail) return;
+
+    const long long s = b * kLagBlock + threadIdx.x;
+    if (s >= G.N) return;
+    int x, y, z;
+    coords(s, G, x, y, z);
+    const int X[3] = {x == 0 ? G.nx - 1 : x - 1, x, x + 1 == G.nx ? 0 : x + 1};
+    const long long Y[3] = {(long long)(y == 0 ? G.ny - 1 : y - 1) * G.nx, (long long)y * G.nx,
+                            (long long)(y + 1 == G.ny ? 0 : y + 1) * G.nx};
+    const long long Z[3] = {(z == 0 ? G.nz - 1 : z - 1) * G.plane, z * G.plane,
+                            (z + 1 == G.nz ? 0 : z + 1) * G.plane};
+    // phi was written during this launch by other CTAs: read it from L2
+    const long long sc = X[1] + Y[1] + Z[1];
+    const T ph = ldcg(phi + sc);
+    const T xp = ldcg(phi + (X[2] + Y[1] + Z[1])), xm = ldcg(phi + (X[0] + Y[1] + Z[1]));
+    const T yp = ldcg(phi + (X[1] + Y[2] + Z[1])), ym = ldcg(phi + (X[1] + Y[0] + Z[1]));
+    const T zp = ldcg(phi + (X[1] + Y[1] + Z[2])), zm = ldcg(phi + (X[1] + Y[1] + Z[0]));
+    const T dx = T(0.5) * (xp - xm), dy = T(0.5) * (yp - ym), dz = T(0.5) * (zp - zm);
+    const T lap = ((xp + xm) + (yp + ym)) + (zp + zm) - T(6) * ph;
+    T f[Q], g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const size_t o = (size_t)i * G.S + (X[1 - cx(i)] + Y[1 - cy(i)] + Z[1 - cz(i)]);
+        f[i] = fa[o];
+        g[i] = ga[o];
+    }
+    collide<T, SH>(p, f, g, ph, dx, dy, dz, lap);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        store(fb + (size_t)i * G.S + sc, f[i]);
+        store(gb + (size_t)i * G.S + sc, g[i]);
+    }
+}
+
+template <typename T, bool SH>
+int run_lag(lb_ctx *c, int nsteps)
+{
+    LGeo G;
+    G.nx = c->p.nx;
+    G.ny = c->p.ny;
+    G.nz = c->p.nz;
+    G.N = c->N;
+    G.S = c->S;
+    G.plane = (long long)c->p.nx * c->p.ny;
+    G.nblocks = (c->N + kLagBlock - 1) / kLagBlock;
+    const long long bpp = (G.plane + kLagBlock - 1) / kLagBlock;   // blocks per plane (rounded up)
+    G.b0 = bpp;
+    const long long slack = c->z_chunk > 0 ? c->z_chunk : kLagSlack;
+    G.D = 3 * bpp + 4 + slack;
+    if (G.D > G.nblocks) G.D = G.nblocks;
+    G.timeout_ns = c->wait_timeout_ns;
+    const long long grid = G.nblocks + G.D;
+    if (grid > 0x7fffffffLL) return LB_ERR_INVALID;
+    const auto p = make_coll<T>(c->p);
+    // every launch starts from zeroed counters (a stream-ordered memset), so
+    // a launch is self-contained and can be captured in a graph and replayed
+    G.ticket_base = 0;
+    G.target = (unsigned long long)G.plane + c->lag_target_skew;
+    const size_t cbytes = (size_t)(G.nz + 1) * sizeof(unsigned long long);
+    for (int t = 0; t < nsteps; t++) {
+        const int a = c->buf.cur, b = 1 - a;
+        int rc = cuda_status(cudaMemsetAsync(c->lag_counters, 0, cbytes, c->stream));
+        if (rc) return rc;
+        k_lag<T, SH><<<(unsigned)grid, kLagBlock, 0, c->stream>>>(
+            (const T *)c->buf.f[a], (const T *)c->buf.g[a], (T *)c->buf.f[b], (T *)c->buf.g[b], (T *)c->phi, p, G,
+            c->lag_counters, c->lag_counters + 1, c->err_flag);
+        rc = check_launch();
+        if (rc) return rc;
+        c->buf.cur = b;
+    }
+    return LB_OK;
+}
+
+}  // namespace
+
+int lag_validate(int block_x, int block_y, int z_chunk)
+{
+    if ((block_x != 0 && block_x != kLagBlock) || (block_y != 0 && block_y != 1)) return LB_ERR_INVALID;
+    if (z_chunk < 0 || z_chunk > (1 << 20)) return LB_ERR_INVALID;
+    return LB_OK;
+}
+
+int launch_step_lag(lb_ctx *c, int nsteps)
+{
+    const int rc = lag_validate(c->block_x, c->block_y, c->z_chunk);
+    if (rc) return rc;
+    return c->p.precision == LB_FP64 ? run_lag<double, false>(c, nsteps) : run_lag<float, true>(c, nsteps);
+}
+
+}  // namespace lbk

@@ -17,7 +17,7 @@ from . import _lib as L
 
 PRECISIONS = {"fp64": L.LB_FP64, "fp32_shifted": L.LB_FP32_SHIFTED}
 KERNELS = {"auto": L.LB_KERNEL_AUTO, "two_pass": L.LB_KERNEL_TWO_PASS, "fused": L.LB_KERNEL_FUSED,
-           "staged": L.LB_KERNEL_STAGED, "slab": L.LB_KERNEL_SLAB}
+           "staged": L.LB_KERNEL_STAGED, "slab": L.LB_KERNEL_SLAB, "lag": L.LB_KERNEL_LAG}
 
 _ALLOC_CB = None
 _FREE_CB = None
@@ -147,6 +147,14 @@ class Lattice:
     def set_kernel(self, kernel="auto", block_x=0, block_y=0, z_chunk=0):
         L.check(L.lib().lb_set_kernel(self.handle, KERNELS[kernel], block_x, block_y, z_chunk),
                 "lb_set_kernel")
+
+    def sync(self):
+        """Wait for queued work; raises LBError(LB_ERR_TIMEOUT) if a bounded
+        device-side wait gave up."""
+        L.check(L.lib().lb_sync(self.handle), "lb_sync")
+
+    def set_wait_timeout(self, seconds: float):
+        L.check(L.lib().lb_set_wait_timeout(self.handle, int(seconds * 1e9)), "lb_set_wait_timeout")
 
     def moments(self, device: bool = False):
         """(rho [N], u [3,N], phi [N]) as numpy (host) or CUDA torch tensors."""

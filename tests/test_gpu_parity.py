@@ -19,7 +19,8 @@ pytestmark = pytest.mark.gpu
 KERNEL_CASES = [("two_pass", (0, 0, 0)), ("fused", (0, 0, 0)), ("fused", (64, 2, 5)),
                 ("fused", (32, 1, 1)), ("fused", (128, 2, 7)), ("staged", (0, 0, 0)),
                 ("staged", (64, 2, 5)), ("staged", (32, 1, 1)), ("staged", (32, 4, 3)),
-                ("slab", (0, 0, 0)), ("slab", (64, 2, 5)), ("slab", (32, 1, 1)), ("slab", (128, 2, 3))]
+                ("slab", (0, 0, 0)), ("slab", (64, 2, 5)), ("slab", (32, 1, 1)), ("slab", (128, 2, 3)),
+                ("lag", (0, 0, 0)), ("lag", (256, 1, 1))]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -90,7 +91,7 @@ def test_kernels_agree(precision):
     out = []
     for kernel, block in (("two_pass", (0, 0, 0)), ("fused", (32, 4, 6)), ("fused", (64, 4, 32)),
                           ("staged", (32, 4, 6)), ("staged", (64, 2, 32)), ("slab", (32, 4, 6)),
-                          ("slab", (64, 4, 2))):
+                          ("slab", (64, 4, 2)), ("lag", (0, 0, 0)), ("lag", (256, 1, 3))):
         with gpu_lattice(dims, p, precision, kernel, block) as lat:
             lat.set_state(to_abi(f0), to_abi(g0))
             lat.step(6)
@@ -180,7 +181,8 @@ def test_nonfinite_state_is_reported():
 TOL_FP32 = {"rho": 1e-9, "u": 1e-7, "phi": 1e-5}
 
 
-@pytest.mark.parametrize("kernel,block", KERNEL_CASES[:3] + KERNEL_CASES[5:7] + KERNEL_CASES[9:11])
+@pytest.mark.parametrize("kernel,block", KERNEL_CASES[:3] + KERNEL_CASES[5:7] + KERNEL_CASES[9:11]
+                         + KERNEL_CASES[13:15])
 def test_spinodal_32cubed_fp32_shifted(kernel, block):
     dims = (32, 32, 32)
     phi0 = L.spinodal_phi0(*dims, seed=0)
@@ -194,14 +196,15 @@ def test_spinodal_32cubed_fp32_shifted(kernel, block):
     _check_moments(got, mo, TOL_FP32, fo)
 
 
-@pytest.mark.parametrize("kernel", ["fused", "staged", "slab"])
+@pytest.mark.parametrize("kernel", ["fused", "staged", "slab", "lag"])
 @pytest.mark.parametrize("dims", [(13, 7, 5), (40, 9, 35), (1, 1, 3)])
 def test_ragged_fp32_shifted_one_step(dims, kernel):
     """One step from a float-representable state: the only difference from
     the FP64 oracle is float arithmetic within the step."""
     p = dict(P0, tau=0.7)
     f0, g0 = nonequilibrium_state(dims, p, seed=80)
-    with gpu_lattice(dims, p, "fp32_shifted", kernel, (32, 2, 3)) as lat:
+    block = (0, 0, 1) if kernel == "lag" else (32, 2, 3)
+    with gpu_lattice(dims, p, "fp32_shifted", kernel, block) as lat:
         lat.set_state(to_abi(f0), to_abi(g0))
         fin, gin = lat.get_state()          # float-rounded input state
         lat.step(1)
@@ -214,3 +217,33 @@ def test_ragged_fp32_shifted_one_step(dims, kernel):
     # shifted value
     assert np.abs(df).max() <= 1e-6 * np.abs(shift).max()
     assert rel(to_oracle(g), go) <= 1e-6
+
+
+# ------------------------------------------------------------------ bounded waits
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_shifted"])
+def test_lagged_kernel_wait_timeout_is_reported_and_recoverable(precision):
+    """The lagged kernel's inter-CTA waits are time-bounded: with targets made
+    unreachable (test hook) every wait gives up, the kernel returns, and the
+    host sees LB_ERR_TIMEOUT; after re-initialisation the context is exact
+    again."""
+    from paper_1405_6162_gb300 import LBError
+    from paper_1405_6162_gb300 import _lib as LL
+    dims = (16, 12, 10)
+    phi0 = L.spinodal_phi0(*dims, seed=11, amp=0.3)
+    (fo, go), mo = _oracle_run(dims, P0, *oracle.init(dims, P0, phi0), 3)
+    with gpu_lattice(dims, P0, precision, "lag", (0, 0, 0)) as lat:
+        lat.set_wait_timeout(0.05)
+        LL.check(LL.lib().lb_debug_wait_skew(lat.handle, 1 << 40), "skew")
+        lat.init(phi0)
+        lat.step(2)
+        with pytest.raises(LBError) as ei:
+            lat.sync()
+        assert ei.value.code == LL.LB_ERR_TIMEOUT
+        lat.sync()                                  # reported once, then cleared
+        LL.check(LL.lib().lb_debug_wait_skew(lat.handle, 0), "skew")
+        lat.init(phi0)
+        lat.step(3)
+        got = lat.moments()
+    tol = TOL_FP64 if precision == "fp64" else TOL_FP32
+    _check_moments(got, mo, tol, fo)
