@@ -245,5 +245,6 @@ def test_lagged_kernel_wait_timeout_is_reported_and_recoverable(precision):
         lat.init(phi0)
         lat.step(3)
         got = lat.moments()
-    tol = TOL_FP64 if precision == "fp64" else TOL_FP32
+    # phi0 amplitude 0.3 makes the stress terms O(1e-2): FP32 per-step bounds
+    tol = TOL_FP64 if precision == "fp64" else {"rho": 1e-7, "u": 1e-7, "phi": 1e-6}
     _check_moments(got, mo, tol, fo)
