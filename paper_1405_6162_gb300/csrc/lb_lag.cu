@@ -8,7 +8,9 @@
 // between a site and its farthest stencil neighbour (one plane up), so every
 // phi a collision needs was produced by a CTA with a lower ticket; completion
 // is published per plane with a counter and awaited with a time-bounded spin
-// (on timeout the CTA records an error flag and returns).  Between the two
+// (on timeout the warp records an error flag and returns).  Publication and
+// waiting are per warp: no CTA-wide barrier or per-thread fence stalls the
+// other warps.  Between the two
 // uses of a g value lie only about D blocks of traffic (~16 MB at 256^3), so
 // the collision's g reads hit L2: DRAM traffic stays near the 76 words per
 // site of the algorithm while every thread keeps the simple one-site,
@@ -62,6 +64,19 @@ __device__ __forceinline__ void coords(long long s, const LGeo &G, int &x, int &
     y = (int)(r - (long long)z * G.ny);
 }
 
+// Adds the number of sites of [first, last] lying in each plane to that
+// plane's counter, after a release fence that makes this warp's phi stores
+// (ordered before it by __syncwarp) visible at GPU scope.
+__device__ __forceinline__ void publish(unsigned long long *plane_done, long long first, long long last,
+                                        long long plane)
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    for (long long pl = first / plane; pl <= last / plane; pl++) {
+        const long long lo = max(first, pl * plane), hi = min(last, (pl + 1) * plane - 1);
+        atomicAdd(plane_done + pl, (unsigned long long)(hi - lo + 1));
+    }
+}
+
 template <typename T, bool SH>
 __global__ void __launch_bounds__(kLagBlock) k_lag(const T *__restrict__ fa, const T *__restrict__ ga,
                                                    T *__restrict__ fb, T *__restrict__ gb, T *phi,
@@ -69,15 +84,13 @@ __global__ void __launch_bounds__(kLagBlock) k_lag(const T *__restrict__ fa, con
                                                    unsigned long long *plane_done, unsigned int *err)
 {
     __shared__ long long s_c;
-    __shared__ int s_fail;
-    if (threadIdx.x == 0) {
-        s_c = (long long)(atomicAdd(ticket, 1ULL) - G.ticket_base);
-        s_fail = 0;
-    }
+    if (threadIdx.x == 0) s_c = (long long)(atomicAdd(ticket, 1ULL) - G.ticket_base);
     __syncthreads();
     const long long c = s_c;
+    const int lane = threadIdx.x & 31;
+    const int wbase = threadIdx.x & ~31;
 
-    // ---- phase 1: phi of block c
+    // ---- phase 1: phi of block c (each warp publishes its own 32 sites)
     if (c < G.nblocks) {
         const long long s = c * kLagBlock + threadIdx.x;
         if (s < G.N) {
@@ -93,47 +106,38 @@ __global__ void __launch_bounds__(kLagBlock) k_lag(const T *__restrict__ fa, con
             for (int i = 0; i < Q; i++) g[i] = ga[(size_t)i * G.S + (X[1 - cx(i)] + Y[1 - cy(i)] + Z[1 - cz(i)])];
             phi[s] = sum19(g);
         }
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const long long first = c * kLagBlock;
-            const long long last = min(first + kLagBlock, G.N) - 1;
-            for (long long pl = first / G.plane; pl <= last / G.plane; pl++) {
-                const long long lo = max(first, pl * G.plane), hi = min(last, (pl + 1) * G.plane - 1);
-                atomicAdd(plane_done + pl, (unsigned long long)(hi - lo + 1));
-            }
-        }
+        __syncwarp();
+        const long long first = c * kLagBlock + wbase;
+        if (lane == 0 && first < G.N) publish(plane_done, first, min(first + 32, G.N) - 1, G.plane);
     }
 
-    // ---- phase 2: collide block b = (c - D + b0) mod nblocks
+    // ---- phase 2: collide block b = (c - D + b0) mod nblocks (per warp, no CTA barrier)
     const long long q = c - G.D;
     if (q < 0) return;
     long long b = q + G.b0;
     if (b >= G.nblocks) b -= G.nblocks;
-    if (threadIdx.x == 0) {
-        const long long first = b * kLagBlock;
-        const long long last = min(first + kLagBlock, G.N) - 1;
+    const long long first = b * kLagBlock + wbase;
+    if (first >= G.N) return;
+    {
+        const long long last = min(first + 32, G.N) - 1;
         const long long p0 = first / G.plane, p1 = last / G.plane;
         const unsigned long long t0 = global_ns();
-        int fail = (*(volatile unsigned int *)err) != 0;   // an earlier CTA already gave up
+        int fail = (*(volatile unsigned int *)err) != 0;   // an earlier wait already gave up
         for (long long k = p0 - 1; k <= p1 + 1 && k - (p0 - 1) < G.nz && !fail; k++) {
             const long long pl = k < 0 ? k + G.nz : (k >= G.nz ? k - G.nz : k);
             while (load_acquire(plane_done + pl) < G.target) {
                 if ((long long)(global_ns() - t0) > G.timeout_ns) {
-                    atomicOr(err, 1u);
+                    if (lane == 0) atomicOr(err, 1u);
                     fail = 1;
                     break;
                 }
-                __nanosleep(128);
+                __nanosleep(64);
             }
         }
-        __threadfence();
-        s_fail = fail;
+        if (__any_sync(0xffffffffu, fail)) return;
     }
-    __syncthreads();
-    if (s_fail) return;
 
-    const long long s = b * kLagBlock + threadIdx.x;
+    const long long s = first + lane;
     if (s >= G.N) return;
     int x, y, z;
     coords(s, G, x, y, z);
