@@ -5,10 +5,11 @@
 // the sum of 19 pulled values A_i(x - c_i); the stencil at x needs phi on the
 // 6 face neighbours, i.e. pulled values up to two sites away.  A CTA owns a
 // block_x x block_y tile of an x-y plane and marches through z_chunk planes
-// (2.5-D blocking).  It keeps phi for planes z-1, z, z+1 over the tile plus a
-// one-site ring in a 3-slot shared-memory ring buffer; each step of the march
-// computes phi one plane ahead (ring sites included), then pulls f and g for
-// plane z, collides and writes the post-collision values at their own sites.
+// (2.5-D blocking).  It keeps phi for planes z-1 .. z+2 over the tile plus a
+// one-site ring in a 4-slot shared-memory ring buffer; each step of the march
+// computes phi two planes ahead (ring sites included) and, in the same phase,
+// pulls f and g for plane z, collides and writes the post-collision values at
+// their own sites, so one barrier per plane separates the phases.
 // Every value of f and g is read from HBM once per timestep and written once
 // (76 words per site); the second pull of g and the ring sites' pulls are
 // L1/L2 hits.  This replaces targetDP's flat TARGET_TLP/VVL strip-mining
@@ -83,10 +84,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxThreads64 : kMaxThreads,
     const int x = x0 + lx, y = y0 + ly;
     const int nhalo = 2 * (ex + ey);
 
-    // phi over the tile and its ring for plane zp into ring slot `slot`
-    auto phi_plane = [&](int zp, int slot) {
-        T *pl = ring + slot * psz;
-        if (active) pl[(ly + 1) * pw + lx + 1] = pulled_phi(ga, G, x, y, zp);
+    // phi of the ring sites of plane zp into ring slot `slot`
+    auto ring_phi = [&](int zp, T *pl) {
         for (int h = tid; h < nhalo; h += nthr) {
             int hx, hy;
             if (h < ex) { hx = h; hy = -1; }
@@ -98,23 +97,38 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxThreads64 : kMaxThreads,
             pl[(hy + 1) * pw + hx + 1] = pulled_phi(ga, G, gx, gy, zp);
         }
     };
+    const int c0 = (ly + 1) * pw + lx + 1;
 
-    phi_plane(wrap_lo(z0 - 1, G.nz), 0);
-    phi_plane(z0, 1);
+    // ring slot of plane z0 - 1 + m is m % 4; prologue: planes z0-1, z0, z0+1
+    for (int m = 0; m < 3; m++) {
+        int zp = z0 - 1 + m;
+        zp = zp < 0 ? zp + G.nz : (zp >= G.nz ? zp - G.nz : zp);
+        zp = zp >= G.nz ? zp - G.nz : zp;
+        T *pl = ring + m * psz;
+        if (active) pl[c0] = pulled_phi(ga, G, x, y, zp);
+        ring_phi(zp, pl);
+    }
+    __syncthreads();
 
     const int X[3] = {wrap_lo(x - 1, G.nx), x, wrap_hi(x + 1, G.nx)};
     const int Y[3] = {wrap_lo(y - 1, G.ny) * G.nx, y * G.nx, wrap_hi(y + 1, G.ny) * G.nx};
     const int plane = G.nx * G.ny;
 
+    // one barrier per plane: phi of plane z+2 and the collision of plane z
+    // are computed in the same phase (their loads are in flight together)
     for (int k = 0; k < ez; k++) {
         const int z = z0 + k;
-        phi_plane(wrap_hi(z + 1, G.nz), (k + 2) % 3);
-        __syncthreads();
+        const bool ahead = k + 1 < ez;                 // plane z+1 is collided next
+        int z2 = z + 2;
+        z2 = z2 >= G.nz ? z2 - G.nz : z2;
+        z2 = z2 >= G.nz ? z2 - G.nz : z2;
+        T *pn = ring + ((k + 3) & 3) * psz;
+        if (ahead) ring_phi(z2, pn);
         if (active) {
-            const T *cm = ring + (k % 3) * psz;
-            const T *cc = ring + ((k + 1) % 3) * psz;
-            const T *cp = ring + ((k + 2) % 3) * psz;
-            const int c0 = (ly + 1) * pw + lx + 1;
+            const T phn = ahead ? pulled_phi(ga, G, x, y, z2) : T(0);
+            const T *cm = ring + (k & 3) * psz;
+            const T *cc = ring + ((k + 1) & 3) * psz;
+            const T *cp = ring + ((k + 2) & 3) * psz;
             const T ph = cc[c0];
             const T xp = cc[c0 + 1], xm = cc[c0 - 1], yp = cc[c0 + pw], ym = cc[c0 - pw];
             const T zp = cp[c0], zm = cm[c0];
@@ -136,6 +150,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxThreads64 : kMaxThreads,
                 store(fb + (size_t)i * G.S + s, f[i]);
                 store(gb + (size_t)i * G.S + s, g[i]);
             }
+            if (ahead) pn[c0] = phn;
         }
         __syncthreads();
     }
@@ -167,7 +182,7 @@ int run(lb_ctx *c, int nsteps)
     const int tiles_y = (G.ny + by - 1) / by;
     const dim3 grid((unsigned)(G.tiles_x * tiles_y), (unsigned)((G.nz + zc - 1) / zc));
     const dim3 block((unsigned)bx, (unsigned)by);
-    const size_t shm = 3 * (size_t)(bx + 2) * (by + 2) * sizeof(T);
+    const size_t shm = 4 * (size_t)(bx + 2) * (by + 2) * sizeof(T);
     const auto p = make_coll<T>(c->p);
     for (int t = 0; t < nsteps; t++) {
         const int a = c->buf.cur, b = 1 - a;

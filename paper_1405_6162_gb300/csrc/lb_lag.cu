@@ -8,9 +8,9 @@
 // between a site and its farthest stencil neighbour (one plane up), so every
 // phi a collision needs was produced by a CTA with a lower ticket; completion
 // is published per plane with a counter and awaited with a time-bounded spin
-// (on timeout the warp records an error flag and returns).  Publication and
-// waiting are per warp: no CTA-wide barrier or per-thread fence stalls the
-// other warps.  Between the two
+// (on timeout the CTA records an error flag and returns).  Each CTA issues
+// one release fence (after its phi stores) and one acquire fence (after its
+// wait), both by a single thread behind a CTA barrier.  Between the two
 // uses of a g value lie only about D blocks of traffic (~16 MB at 256^3), so
 // the collision's g reads hit L2: DRAM traffic stays near the 76 words per
 // site of the algorithm while every thread keeps the simple one-site,
@@ -46,13 +46,6 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-__device__ __forceinline__ unsigned long long load_acquire(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
 template <typename T>
 __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 
@@ -64,17 +57,11 @@ __device__ __forceinline__ void coords(long long s, const LGeo &G, int &x, int &
     y = (int)(r - (long long)z * G.ny);
 }
 
-// Adds the number of sites of [first, last] lying in each plane to that
-// plane's counter, after a release fence that makes this warp's phi stores
-// (ordered before it by __syncwarp) visible at GPU scope.
-__device__ __forceinline__ void publish(unsigned long long *plane_done, long long first, long long last,
-                                        long long plane)
+__device__ __forceinline__ unsigned long long load_relaxed(const unsigned long long *p)
 {
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
-    for (long long pl = first / plane; pl <= last / plane; pl++) {
-        const long long lo = max(first, pl * plane), hi = min(last, (pl + 1) * plane - 1);
-        atomicAdd(plane_done + pl, (unsigned long long)(hi - lo + 1));
-    }
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
 template <typename T, bool SH>
@@ -84,13 +71,15 @@ __global__ void __launch_bounds__(kLagBlock) k_lag(const T *__restrict__ fa, con
                                                    unsigned long long *plane_done, unsigned int *err)
 {
     __shared__ long long s_c;
-    if (threadIdx.x == 0) s_c = (long long)(atomicAdd(ticket, 1ULL) - G.ticket_base);
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) {
+        s_c = (long long)(atomicAdd(ticket, 1ULL) - G.ticket_base);
+        s_fail = 0;
+    }
     __syncthreads();
     const long long c = s_c;
-    const int lane = threadIdx.x & 31;
-    const int wbase = threadIdx.x & ~31;
 
-    // ---- phase 1: phi of block c (each warp publishes its own 32 sites)
+    // ---- phase 1: phi of block c, published with one release per CTA
     if (c < G.nblocks) {
         const long long s = c * kLagBlock + threadIdx.x;
         if (s < G.N) {
@@ -106,36 +95,50 @@ __global__ void __launch_bounds__(kLagBlock) k_lag(const T *__restrict__ fa, con
             for (int i = 0; i < Q; i++) g[i] = ga[(size_t)i * G.S + (X[1 - cx(i)] + Y[1 - cy(i)] + Z[1 - cz(i)])];
             phi[s] = sum19(g);
         }
-        __syncwarp();
-        const long long first = c * kLagBlock + wbase;
-        if (lane == 0 && first < G.N) publish(plane_done, first, min(first + 32, G.N) - 1, G.plane);
+        // the barrier orders every thread's phi store before thread 0's
+        // release fence (fences are cumulative), which precedes the counts
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
+            const long long first = c * kLagBlock;
+            const long long last = min(first + kLagBlock, G.N) - 1;
+            for (long long pl = first / G.plane; pl <= last / G.plane; pl++) {
+                const long long lo = max(first, pl * G.plane), hi = min(last, (pl + 1) * G.plane - 1);
+                atomicAdd(plane_done + pl, (unsigned long long)(hi - lo + 1));
+            }
+        }
     }
 
-    // ---- phase 2: collide block b = (c - D + b0) mod nblocks (per warp, no CTA barrier)
+    // ---- phase 2: collide block b = (c - D + b0) mod nblocks
     const long long q = c - G.D;
     if (q < 0) return;
     long long b = q + G.b0;
     if (b >= G.nblocks) b -= G.nblocks;
-    const long long first = b * kLagBlock + wbase;
-    if (first >= G.N) return;
-    {
-        const long long last = min(first + 32, G.N) - 1;
+    if (threadIdx.x == 0) {
+        const long long first = b * kLagBlock;
+        const long long last = min(first + kLagBlock, G.N) - 1;
         const long long p0 = first / G.plane, p1 = last / G.plane;
         const unsigned long long t0 = global_ns();
         int fail = (*(volatile unsigned int *)err) != 0;   // an earlier wait already gave up
         for (long long k = p0 - 1; k <= p1 + 1 && k - (p0 - 1) < G.nz && !fail; k++) {
             const long long pl = k < 0 ? k + G.nz : (k >= G.nz ? k - G.nz : k);
-            while (load_acquire(plane_done + pl) < G.target) {
+            while (load_relaxed(plane_done + pl) < G.target) {
                 if ((long long)(global_ns() - t0) > G.timeout_ns) {
-                    if (lane == 0) atomicOr(err, 1u);
+                    atomicOr(err, 1u);
                     fail = 1;
                     break;
                 }
                 __nanosleep(64);
             }
         }
-        if (__any_sync(0xffffffffu, fail)) return;
+        // acquire: the phi reads below are ordered after the counts seen
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        s_fail = fail;
     }
+    __syncthreads();
+    if (s_fail) return;
+    const long long first = b * kLagBlock;
+    const int lane = threadIdx.x;
 
     const long long s = first + lane;
     if (s >= G.N) return;
