@@ -174,7 +174,7 @@ int lb_set_state(lb_ctx *c, const double *f, const double *g, int ptr_kind);
  * block_y threads per CTA and z_chunk planes per CTA of the fused, staged
  * and slab kernels (0 = library default for any of the three).  For
  * LB_KERNEL_LAG block_x must be 0 or 256, block_y 0 or 1, and z_chunk is the
- * lag slack in site blocks beyond the stencil's reach (0 = default 8).  Validated against the
+ * lag slack in site blocks beyond the stencil's reach (0 = default 128).  Validated against the
  * kernel's limits; LB_ERR_INVALID otherwise.  Paper: the tunable VVL and TPB
  * of TARGET_TLP / TARGET_LAUNCH, Sec. III.C. */
 int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk);

@@ -53,7 +53,7 @@ struct lb_ctx {
 namespace lbk {
 
 constexpr int kLagBlock = 256;       // sites per block of the lagged kernel
-constexpr long long kLagSlack = 8;    // extra lag (blocks) beyond the stencil reach
+constexpr long long kLagSlack = 128;  // extra lag (blocks) beyond the stencil reach
 constexpr int kReduceBlocks = 608;   // 4 x 152 SMs; fixed so sums are reproducible
 constexpr int kReduceThreads = 256;
 

@@ -3,8 +3,9 @@
 // Sites are cut into blocks of kLagBlock consecutive indices (one CTA each).
 // The CTA holding ticket c (tickets are taken from a global counter when the
 // CTA starts, so a lower ticket always belongs to a CTA that has already
-// started) first computes phi = sum of the 19 pulled g values for block c and
-// stores it, then collides block c - D.  D exceeds the distance in blocks
+// started) computes phi = sum of the 19 pulled g values for block c and, in
+// the same phase, collides block c - D; it publishes block c's phi at its
+// end.  D exceeds the distance in blocks
 // between a site and its farthest stencil neighbour (one plane up), so every
 // phi a collision needs was produced by a CTA with a lower ticket; completion
 // is published per plane with a counter and awaited with a time-bounded spin
@@ -64,6 +65,23 @@ __device__ __forceinline__ unsigned long long load_relaxed(const unsigned long l
     return v;
 }
 
+// Periodic neighbourhood of site s, pre-multiplied by the row/plane strides.
+struct LNbr {
+    int X[3];
+    long long Y[3], Z[3];
+    __device__ __forceinline__ LNbr(long long s, const LGeo &G)
+    {
+        int x, y, z;
+        coords(s, G, x, y, z);
+        X[0] = x == 0 ? G.nx - 1 : x - 1; X[1] = x; X[2] = x + 1 == G.nx ? 0 : x + 1;
+        Y[0] = (long long)(y == 0 ? G.ny - 1 : y - 1) * G.nx; Y[1] = (long long)y * G.nx;
+        Y[2] = (long long)(y + 1 == G.ny ? 0 : y + 1) * G.nx;
+        Z[0] = (z == 0 ? G.nz - 1 : z - 1) * G.plane; Z[1] = z * G.plane;
+        Z[2] = (z + 1 == G.nz ? 0 : z + 1) * G.plane;
+    }
+    __device__ __forceinline__ long long src(int i) const { return X[1 - cx(i)] + Y[1 - cy(i)] + Z[1 - cz(i)]; }
+};
+
 template <typename T, bool SH>
 __global__ void __launch_bounds__(kLagBlock) k_lag(const T *__restrict__ fa, const T *__restrict__ ga,
                                                    T *__restrict__ fb, T *__restrict__ gb, T *phi,
@@ -78,43 +96,13 @@ __global__ void __launch_bounds__(kLagBlock) k_lag(const T *__restrict__ fa, con
     }
     __syncthreads();
     const long long c = s_c;
-
-    // ---- phase 1: phi of block c, published with one release per CTA
-    if (c < G.nblocks) {
-        const long long s = c * kLagBlock + threadIdx.x;
-        if (s < G.N) {
-            int x, y, z;
-            coords(s, G, x, y, z);
-            const int X[3] = {x == 0 ? G.nx - 1 : x - 1, x, x + 1 == G.nx ? 0 : x + 1};
-            const long long Y[3] = {(long long)(y == 0 ? G.ny - 1 : y - 1) * G.nx, (long long)y * G.nx,
-                                    (long long)(y + 1 == G.ny ? 0 : y + 1) * G.nx};
-            const long long Z[3] = {(z == 0 ? G.nz - 1 : z - 1) * G.plane, z * G.plane,
-                                    (z + 1 == G.nz ? 0 : z + 1) * G.plane};
-            T g[Q];
-#pragma unroll
-            for (int i = 0; i < Q; i++) g[i] = ga[(size_t)i * G.S + (X[1 - cx(i)] + Y[1 - cy(i)] + Z[1 - cz(i)])];
-            phi[s] = sum19(g);
-        }
-        // the barrier orders every thread's phi store before thread 0's
-        // release fence (fences are cumulative), which precedes the counts
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            asm volatile("fence.acq_rel.gpu;" ::: "memory");
-            const long long first = c * kLagBlock;
-            const long long last = min(first + kLagBlock, G.N) - 1;
-            for (long long pl = first / G.plane; pl <= last / G.plane; pl++) {
-                const long long lo = max(first, pl * G.plane), hi = min(last, (pl + 1) * G.plane - 1);
-                atomicAdd(plane_done + pl, (unsigned long long)(hi - lo + 1));
-            }
-        }
-    }
-
-    // ---- phase 2: collide block b = (c - D + b0) mod nblocks
     const long long q = c - G.D;
-    if (q < 0) return;
     long long b = q + G.b0;
     if (b >= G.nblocks) b -= G.nblocks;
-    if (threadIdx.x == 0) {
+    const bool produce = c < G.nblocks, consume = q >= 0;
+
+    // wait until every plane the collision of block b reads phi from is done
+    if (consume && threadIdx.x == 0) {
         const long long first = b * kLagBlock;
         const long long last = min(first + kLagBlock, G.N) - 1;
         const long long p0 = first / G.plane, p1 = last / G.plane;
@@ -136,39 +124,60 @@ __global__ void __launch_bounds__(kLagBlock) k_lag(const T *__restrict__ fa, con
         s_fail = fail;
     }
     __syncthreads();
-    if (s_fail) return;
-    const long long first = b * kLagBlock;
-    const int lane = threadIdx.x;
 
-    const long long s = first + lane;
-    if (s >= G.N) return;
-    int x, y, z;
-    coords(s, G, x, y, z);
-    const int X[3] = {x == 0 ? G.nx - 1 : x - 1, x, x + 1 == G.nx ? 0 : x + 1};
-    const long long Y[3] = {(long long)(y == 0 ? G.ny - 1 : y - 1) * G.nx, (long long)y * G.nx,
-                            (long long)(y + 1 == G.ny ? 0 : y + 1) * G.nx};
-    const long long Z[3] = {(z == 0 ? G.nz - 1 : z - 1) * G.plane, z * G.plane,
-                            (z + 1 == G.nz ? 0 : z + 1) * G.plane};
-    // phi was written during this launch by other CTAs: read it from L2
-    const long long sc = X[1] + Y[1] + Z[1];
-    const T ph = ldcg(phi + sc);
-    const T xp = ldcg(phi + (X[2] + Y[1] + Z[1])), xm = ldcg(phi + (X[0] + Y[1] + Z[1]));
-    const T yp = ldcg(phi + (X[1] + Y[2] + Z[1])), ym = ldcg(phi + (X[1] + Y[0] + Z[1]));
-    const T zp = ldcg(phi + (X[1] + Y[1] + Z[2])), zm = ldcg(phi + (X[1] + Y[1] + Z[0]));
-    const T dx = T(0.5) * (xp - xm), dy = T(0.5) * (yp - ym), dz = T(0.5) * (zp - zm);
-    const T lap = ((xp + xm) + (yp + ym)) + (zp + zm) - T(6) * ph;
-    T f[Q], g[Q];
+    // phi of block c and the collision of block b in one phase: the 19 phi
+    // loads and the 38 + 7 collision loads of a thread are in flight together
+    const long long sp = c * kLagBlock + threadIdx.x;
+    const long long sb = b * kLagBlock + threadIdx.x;
+    const bool do_phi = produce && sp < G.N;
+    const bool do_col = consume && !s_fail && sb < G.N;
+    T phv = T(0);
+    if (do_phi) {
+        const LNbr n(sp, G);
+        T g[Q];
 #pragma unroll
-    for (int i = 0; i < Q; i++) {
-        const size_t o = (size_t)i * G.S + (X[1 - cx(i)] + Y[1 - cy(i)] + Z[1 - cz(i)]);
-        f[i] = fa[o];
-        g[i] = ga[o];
+        for (int i = 0; i < Q; i++) g[i] = ga[(size_t)i * G.S + n.src(i)];
+        phv = sum19(g);
     }
-    collide<T, SH>(p, f, g, ph, dx, dy, dz, lap);
+    if (do_col) {
+        const LNbr n(sb, G);
+        // phi was written during this launch by other CTAs: read it from L2
+        const long long sc = n.X[1] + n.Y[1] + n.Z[1];
+        const T ph = ldcg(phi + sc);
+        const T xp = ldcg(phi + (n.X[2] + n.Y[1] + n.Z[1])), xm = ldcg(phi + (n.X[0] + n.Y[1] + n.Z[1]));
+        const T yp = ldcg(phi + (n.X[1] + n.Y[2] + n.Z[1])), ym = ldcg(phi + (n.X[1] + n.Y[0] + n.Z[1]));
+        const T zp = ldcg(phi + (n.X[1] + n.Y[1] + n.Z[2])), zm = ldcg(phi + (n.X[1] + n.Y[1] + n.Z[0]));
+        T f[Q], g[Q];
 #pragma unroll
-    for (int i = 0; i < Q; i++) {
-        store(fb + (size_t)i * G.S + sc, f[i]);
-        store(gb + (size_t)i * G.S + sc, g[i]);
+        for (int i = 0; i < Q; i++) {
+            const size_t o = (size_t)i * G.S + n.src(i);
+            f[i] = fa[o];
+            g[i] = ga[o];
+        }
+        const T dx = T(0.5) * (xp - xm), dy = T(0.5) * (yp - ym), dz = T(0.5) * (zp - zm);
+        const T lap = ((xp + xm) + (yp + ym)) + (zp + zm) - T(6) * ph;
+        collide<T, SH>(p, f, g, ph, dx, dy, dz, lap);
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            store(fb + (size_t)i * G.S + sc, f[i]);
+            store(gb + (size_t)i * G.S + sc, g[i]);
+        }
+    }
+    if (do_phi) phi[sp] = phv;
+
+    // publish block c: the barrier orders every thread's phi store before
+    // thread 0's release fence (fences are cumulative), then the counts
+    if (produce) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
+            const long long first = c * kLagBlock;
+            const long long last = min(first + kLagBlock, G.N) - 1;
+            for (long long pl = first / G.plane; pl <= last / G.plane; pl++) {
+                const long long lo = max(first, pl * G.plane), hi = min(last, (pl + 1) * G.plane - 1);
+                atomicAdd(plane_done + pl, (unsigned long long)(hi - lo + 1));
+            }
+        }
     }
 }
 
