@@ -267,7 +267,7 @@ int lb_step(lb_ctx *c, int nsteps)
 {
     if (!c || nsteps < 0) return LB_ERR_INVALID;
     if (nsteps == 0) return LB_OK;
-    if (c->kernel == LB_KERNEL_TWO_PASS) return lbk::launch_step_two_pass(c, nsteps);
+    if (c->kernel == LB_KERNEL_TWO_PASS || c->kernel == LB_KERNEL_AUTO) return lbk::launch_step_two_pass(c, nsteps);
     if (c->kernel == LB_KERNEL_STAGED) return lbk::launch_step_staged(c, nsteps);
     if (c->kernel == LB_KERNEL_SLAB) return lbk::launch_step_slab(c, nsteps);
     if (c->kernel == LB_KERNEL_LAG) return lbk::launch_step_lag(c, nsteps);
@@ -288,7 +288,7 @@ int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk)
     } else if (kernel == LB_KERNEL_SLAB) {
         int rc = lbk::slab_validate(c->p.precision, block_x, block_y, z_chunk);
         if (rc) return rc;
-    } else if (kernel != LB_KERNEL_TWO_PASS) {
+    } else if (kernel == LB_KERNEL_FUSED) {
         int rc = lbk::fused_validate(c->p.precision, block_x, block_y, z_chunk);
         if (rc) return rc;
     }

@@ -18,7 +18,7 @@ import time
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 # (kernel, block_x, block_y, z_chunk); 0 = library default
-DEFAULT = ("fused", 0, 0, 0)
+DEFAULT = ("auto", 0, 0, 0)
 
 
 def _gpu_name() -> str:
