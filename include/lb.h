@@ -200,6 +200,32 @@ int lb_set_wait_timeout(lb_ctx *c, long long timeout_ns);
  * counterpart. */
 int lb_debug_wait_skew(lb_ctx *c, unsigned long long skew);
 
+/* One FP64 timestep that allocates no device memory, for callers that
+ * cannot allocate: a host application whose device memory is entirely
+ * reserved by its own allocator, or a latency-critical loop that must never
+ * enter cudaMalloc/cudaFree (which can block the whole device).  The paper
+ * has no counterpart.
+ *   p       lattice and model parameters; p->precision must be LB_FP64 and
+ *           nx*ny*nz at most 262144 (64^3), else LB_ERR_INVALID.
+ *   fa, ga  input: device double[19][N] (ABI velocity order, site s =
+ *           x + nx*(y + ny*z)) holding the post-collision values of the
+ *           previous timestep, i.e. the post-streaming state is
+ *           f_i(x, t) = fa[i*N + site(x - c_i)] (likewise g).
+ *   fb, gb  output, same layout and convention for time t+1; must not
+ *           alias the inputs (LB_ERR_INVALID).
+ *   cuda_stream  stream the work is queued on (NULL = legacy default);
+ *           the call returns before the work runs.
+ * The arithmetic is lb_step's two-pass kernel pair.  The order parameter
+ * between the two passes lives in one fixed device array of 262144 doubles
+ * (2 MiB) inside the library, held by every GPU that loads it until the
+ * process exits and shared by all calls: calls that overlap on the GPU race
+ * on it.  Each call writes every value of it that it reads, so nothing needs
+ * clearing between calls.  The first call on a device looks up that array's
+ * device address (set-up); make that first call before any stream capture.
+ * Errors: LB_ERR_INVALID, LB_ERR_CUDA. */
+int lb_step_fp64_noalloc(const lb_params *p, const double *fa, const double *ga, double *fb, double *gb,
+                         void *cuda_stream);
+
 /* Extents and precision of c (any output may be NULL). */
 int lb_get_info(const lb_ctx *c, int *nx, int *ny, int *nz, int *precision);
 

@@ -63,6 +63,7 @@ SIGNATURES = {
     "lb_sync": (_I, [_P]),
     "lb_set_wait_timeout": (_I, [_P, ctypes.c_longlong]),
     "lb_debug_wait_skew": (_I, [_P, ctypes.c_ulonglong]),
+    "lb_step_fp64_noalloc": (_I, [ctypes.POINTER(lb_params), _P, _P, _P, _P, _P]),
     "lb_strerror": (ctypes.c_char_p, [_I]),
     "lb_last_error": (ctypes.c_char_p, []),
 }

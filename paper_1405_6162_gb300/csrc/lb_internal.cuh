@@ -89,6 +89,10 @@ int check_launch();
 // launchers (lb_kernels.cu); each returns an LB_* code
 int launch_init(lb_ctx *c, const double *phi0_d, const double *u0_d);
 int launch_step_two_pass(lb_ctx *c, int nsteps);
+// one FP64 two-pass timestep on raw buffers (component stride S, phi scratch
+// of N doubles supplied by the caller)
+int launch_two_pass_fp64_raw(const lb_params &p, const double *fa, const double *ga, double *phi, double *fb,
+                             double *gb, long long S, cudaStream_t stream);
 int launch_moments(lb_ctx *c, double *rho, double *u, double *phi);
 int launch_get_state(lb_ctx *c, double *f, double *g);
 int launch_set_state(lb_ctx *c, const double *f, const double *g);

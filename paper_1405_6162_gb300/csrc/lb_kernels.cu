@@ -299,6 +299,17 @@ static int two_pass(lb_ctx *c, int nsteps)
     return LB_OK;
 }
 
+int launch_two_pass_fp64_raw(const lb_params &prm, const double *fa, const double *ga, double *phi, double *fb,
+                             double *gb, long long S, cudaStream_t stream)
+{
+    const auto p = make_coll<double>(prm);
+    const long long N = (long long)prm.nx * prm.ny * prm.nz;
+    const unsigned grid = grid_for(N, 256);
+    k_phi_pull<double><<<grid, 256, 0, stream>>>(ga, phi, prm.nx, prm.ny, prm.nz, S);
+    k_collide_pull<double, false><<<grid, 256, 0, stream>>>(fa, ga, phi, fb, gb, p, prm.nx, prm.ny, prm.nz, S);
+    return check_launch();
+}
+
 int launch_step_two_pass(lb_ctx *c, int nsteps)
 {
     return c->p.precision == LB_FP64 ? two_pass<double, false>(c, nsteps) : two_pass<float, true>(c, nsteps);
