@@ -39,6 +39,10 @@ ORACLE_SAMPLE = (64, 64, 64)
 ORACLE_STEPS = 30
 E2E_STEPS = 50
 FALLBACK_HBM = 6800.0
+# kernels one timestep launches, per lb_set_kernel choice
+STEP_KERNELS = {"auto": "timestep = k_phi_pull + k_collide_pull (two launches)",
+                "two_pass": "timestep = k_phi_pull + k_collide_pull (two launches)",
+                "fused": "k_fused", "staged": "k_staged", "slab": "k_slab", "lag": "k_lag"}
 
 
 def _dist():
@@ -67,19 +71,20 @@ def _kernel_sha():
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic(precision):
-    """DRAM bytes per launch of the fused kernel from the committed ncu
-    summary, if it was taken on the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", f"fused_step_{precision}_256cubed.md")
+def _profile_value(name, key, need_current=True):
+    """A number recorded in a committed ncu summary (profiles/<name>.md, a
+    line "key: value"); None if absent or, when ``need_current``, if the
+    summary was taken on other kernel sources than the current ones."""
+    path = os.path.join(ROOT, "profiles", f"{name}.md")
     try:
         txt = open(path).read()
     except OSError:
         return None
     m_sha = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", txt)
-    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not (m_sha and m_b) or m_sha.group(1) != _kernel_sha():
+    m_v = re.search(rf"^{re.escape(key)}:\s*([0-9.eE+-]+)", txt, re.M)
+    if not m_v or (need_current and (not m_sha or m_sha.group(1) != _kernel_sha())):
         return None
-    return float(m_b.group(1))
+    return float(m_v.group(1))
 
 
 class Clocks:
@@ -256,11 +261,24 @@ def run_ours(args):
     def line_for(prec):
         r = results[prec]
         mlups = ws * n * args.steps / r["wall"] / 1e6
-        achieved = BYTES_PER_SITE[prec] * n / r["t_launch"] / 1e9
-        traffic = _ncu_traffic(prec)
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                "algorithmic_bytes_per_launch": BYTES_PER_SITE[prec] * n}
+        kernel = STEP_KERNELS.get(r["cfg"][0], r["cfg"][0])
+        prof = f"step_{prec}_256cubed"
+        if prec == "fp32_shifted":
+            achieved = BYTES_PER_SITE[prec] * n / r["t_launch"] / 1e9
+            roof = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": _profile_value(prof, "dram_bytes_per_step"),
+                    "peak_kind": f"{peak_kind} (copy bandwidth)",
+                    "algorithmic_bytes_per_launch": BYTES_PER_SITE[prec] * n}
+        else:
+            # FP64 is bound by the FP64 pipe: flops per site from ncu counters
+            fl = _profile_value(prof, "fp64_flops_per_site")
+            pk = _profile_value(prof, "fp64_peak_tflops", need_current=False)
+            achieved = fl * n / r["t_launch"] / 1e12 if fl else None
+            roof = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                    "frac": (achieved / pk) if (achieved and pk) else None,
+                    "traffic": _profile_value(prof, "dram_bytes_per_step"),
+                    "peak_kind": "measured FP64 FMA throughput (profiles/step_fp64_256cubed.md)",
+                    "hbm_frac": BYTES_PER_SITE[prec] * n / r["t_launch"] / 1e9 / peak}
         return mlups, roof
 
     v32, roof32 = line_for("fp32_shifted")
@@ -286,7 +304,7 @@ def run_ours(args):
                                        "max|gpu-oracle| / max|oracle| per field (u: / max sum_i|f_i c_i|/rho)", **errs} if errs else None),
         "clocks": r32["clocks"],
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (2 if r32["cfg"][0] in ("auto", "two_pass") else 1),
         "cpu_baseline": cpu,
     }
     print(json.dumps(out))
