@@ -226,6 +226,57 @@ int lb_debug_wait_skew(lb_ctx *c, unsigned long long skew);
 int lb_step_fp64_noalloc(const lb_params *p, const double *fa, const double *ga, double *fb, double *gb,
                          void *cuda_stream);
 
+/* ---- Ensembles: many independent lattices in one persistent launch ----
+ * An ensemble holds n lattices of any extents and parameters (one precision
+ * for all).  lb_batch_run advances every lattice by nsteps timesteps with
+ * one cooperative (co-resident) kernel launch that loops over the steps and
+ * over a (lattice, block of sites) work list, with a grid-wide barrier
+ * between the phi pass and the collide/stream pass; the launch is captured
+ * in a CUDA graph (one per step count and parity) and replayed.  Per-site
+ * arithmetic is exactly lb_step's.  Paper: the tunable thread-block size
+ * TPB and per-thread work of TARGET_LAUNCH / TARGET_TLP, Sec. III.C. */
+typedef struct lb_batch lb_batch;
+
+/* Create an ensemble of n lattices with parameters p[0..n-1] (same
+ * precision), work ordered after cuda_stream.  Errors as lb_create. */
+int lb_batch_create(int n, const lb_params *p, void *cuda_stream, lb_batch **out);
+
+/* Free the ensemble and all its lattices (NULL is a no-op). */
+void lb_batch_destroy(lb_batch *b);
+
+/* Lattice k of the ensemble as a context for lb_init, lb_moments,
+ * lb_reduce, lb_get_state, lb_set_state and lb_sync (NULL if k is out of
+ * range).  It belongs to the ensemble: lb_step on it returns LB_ERR_INVALID
+ * and lb_destroy ignores it. */
+lb_ctx *lb_batch_lattice(lb_batch *b, int k);
+
+/* Advance every lattice by nsteps (>= 0), asynchronously after the work
+ * queued on the ensemble's stream.  Errors: LB_ERR_INVALID, LB_ERR_CUDA;
+ * a grid barrier that timed out is reported by lb_batch_sync (or lb_sync
+ * of any member) as LB_ERR_TIMEOUT, after which the states are invalid
+ * until re-initialised. */
+int lb_batch_run(lb_batch *b, int nsteps);
+
+/* Synchronise; LB_ERR_TIMEOUT if a grid barrier gave up since the last
+ * check (the flag is then cleared). */
+int lb_batch_sync(lb_batch *b);
+
+/* Launch shape: threads per CTA (= sites per work item; multiple of 32, at
+ * most 512, 256 in FP64) and CTAs per SM (0 = as many as fit; the grid is
+ * always co-resident).  Paper: TPB and VVL tuning, Sec. III.C and IV. */
+int lb_batch_set_launch(lb_batch *b, int threads, int ctas_per_sm);
+
+/* n lattices, work items per pass, CTAs in the grid, threads per CTA. */
+int lb_batch_size(const lb_batch *b, int *n, int *work_items, int *grid, int *threads);
+
+/* Bound (ns) of every grid-barrier wait (default 1e9). */
+int lb_batch_set_wait_timeout(lb_batch *b, long long timeout_ns);
+
+/* Test hook: CTA 0 leaves before the first grid barrier, so every other
+ * CTA's wait runs into its time bound (the timeout path without a GPU
+ * fault).  0 restores normal operation.  Paper: no counterpart. */
+int lb_batch_debug_skip_arrival(lb_batch *b, int enable);
+
 /* Extents and precision of c (any output may be NULL). */
 int lb_get_info(const lb_ctx *c, int *nx, int *ny, int *nz, int *precision);
 

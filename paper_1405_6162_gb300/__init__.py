@@ -8,3 +8,4 @@ This package only marshals arguments to that library.
 from .nvbuild import build, library_path  # noqa: F401
 from .lattice import KERNELS, PRECISIONS, VELOCITIES, Lattice, use_torch_allocator  # noqa: F401
 from ._lib import LBError  # noqa: F401
+from .batch import Batch  # noqa: F401

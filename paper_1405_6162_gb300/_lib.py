@@ -64,6 +64,15 @@ SIGNATURES = {
     "lb_set_wait_timeout": (_I, [_P, ctypes.c_longlong]),
     "lb_debug_wait_skew": (_I, [_P, ctypes.c_ulonglong]),
     "lb_step_fp64_noalloc": (_I, [ctypes.POINTER(lb_params), _P, _P, _P, _P, _P]),
+    "lb_batch_create": (_I, [_I, ctypes.POINTER(lb_params), _P, ctypes.POINTER(_P)]),
+    "lb_batch_destroy": (None, [_P]),
+    "lb_batch_lattice": (_P, [_P, _I]),
+    "lb_batch_run": (_I, [_P, _I]),
+    "lb_batch_sync": (_I, [_P]),
+    "lb_batch_set_launch": (_I, [_P, _I, _I]),
+    "lb_batch_size": (_I, [_P, _P, _P, _P, _P]),
+    "lb_batch_set_wait_timeout": (_I, [_P, ctypes.c_longlong]),
+    "lb_batch_debug_skip_arrival": (_I, [_P, _I]),
     "lb_strerror": (ctypes.c_char_p, [_I]),
     "lb_last_error": (ctypes.c_char_p, []),
 }

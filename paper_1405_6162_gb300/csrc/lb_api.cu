@@ -59,7 +59,7 @@ void free_all(lb_ctx *c)
     dev_free(c, c->partial, (size_t)lbk::kReduceBlocks * 5 * sizeof(double));
     dev_free(c, c->dev_out, 8 * sizeof(double));
     dev_free(c, c->lag_counters, (size_t)(c->p.nz + 1) * sizeof(unsigned long long));
-    dev_free(c, c->err_flag, sizeof(unsigned int));
+    if (!c->batch_owned) dev_free(c, c->err_flag, sizeof(unsigned int));
     c->lag_counters = nullptr;
     c->err_flag = nullptr;
     c->phi = nullptr;
@@ -125,6 +125,20 @@ int cuda_status(cudaError_t e)
 }
 
 int check_launch() { return cuda_status(cudaGetLastError()); }
+
+void adopt_into_batch(lb_ctx *c, unsigned int *shared_err)
+{
+    cudaStreamSynchronize(c->stream);
+    dev_free(c, c->err_flag, sizeof(unsigned int));
+    c->err_flag = shared_err;
+    c->batch_owned = 1;
+}
+
+void release_from_batch(lb_ctx *c)
+{
+    c->err_flag = nullptr;
+    c->batch_owned = 0;
+}
 
 }  // namespace lbk
 
@@ -212,7 +226,7 @@ int lb_create(const lb_params *p, void *cuda_stream, lb_ctx **out)
 
 void lb_destroy(lb_ctx *c)
 {
-    if (!c) return;
+    if (!c || c->batch_owned) return;   // ensemble members are freed by lb_batch_destroy
     cudaStreamSynchronize(c->stream);
     cudaGetLastError();
     free_all(c);
@@ -265,7 +279,7 @@ int lb_init(lb_ctx *c, const double *phi0, const double *u0, int ptr_kind)
 
 int lb_step(lb_ctx *c, int nsteps)
 {
-    if (!c || nsteps < 0) return LB_ERR_INVALID;
+    if (!c || nsteps < 0 || c->batch_owned) return LB_ERR_INVALID;
     if (nsteps == 0) return LB_OK;
     if (c->kernel == LB_KERNEL_TWO_PASS || c->kernel == LB_KERNEL_AUTO) return lbk::launch_step_two_pass(c, nsteps);
     if (c->kernel == LB_KERNEL_STAGED) return lbk::launch_step_staged(c, nsteps);

@@ -1,0 +1,384 @@
+// lb_batch.cu -- an ensemble of independent lattices (uneven extents and
+// parameters) advanced by one persistent launch, captured in a CUDA graph.
+//
+// Every lattice is an ordinary context (its own buffers and parameters).  The
+// work of one timestep over the whole ensemble is a list of (lattice, block
+// of sites) items; a grid of CTAs that all fit on the GPU at once (a
+// cooperative launch) walks that list twice per timestep -- the phi pass,
+// then the collide/stream pass -- with a grid-wide barrier after each, and
+// loops over the timesteps inside the kernel.  The per-site arithmetic is the
+// default step's (lb_site.cuh).  The launch (with a reset of the barrier
+// state) is captured once per (steps, parity) into a CUDA graph and replayed.
+// The block size and CTAs per SM -- the paper's TPB and its per-thread work
+// (targetDP Sec. III.C) -- are the knobs the autotuner sets.
+#include <cuda_runtime.h>
+
+#include <map>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "d3q19.cuh"
+#include "lb_internal.cuh"
+#include "lb_site.cuh"
+
+namespace lbk {
+
+namespace {
+
+constexpr int kBatchMaxThreads = 512;     // FP32 CTA size limit
+constexpr int kBatchMaxThreads64 = 256;   // FP64: more registers per thread
+
+template <typename T>
+struct LatDesc {
+    int nx, ny, nz;
+    long long N, S;
+    const T *f[2];
+    const T *g[2];
+    T *phi;
+    Coll<T> p;
+};
+
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+};
+
+__device__ __forceinline__ unsigned long long batch_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of a co-resident grid.  Time-bounded: a CTA that waits
+// longer than timeout_ns (or sees that another CTA already gave up) sets the
+// error flag and returns false instead of hanging.
+__device__ bool grid_sync(GridBarrier *bar, unsigned int nblocks, long long timeout_ns, unsigned int *err,
+                          int *s_fail)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *vgen = &bar->gen;
+        const unsigned int gen = *vgen;
+        __threadfence();
+        int fail = 0;
+        if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            const unsigned long long t0 = batch_ns();
+            while (*vgen == gen) {
+                if (*(volatile unsigned int *)err || (long long)(batch_ns() - t0) > timeout_ns) {
+                    atomicOr(err, 1u);
+                    fail = 1;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        *s_fail = fail;
+    }
+    __syncthreads();
+    return !*s_fail;
+}
+
+template <typename T, bool SH>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? kBatchMaxThreads64 : kBatchMaxThreads) k_batch(const LatDesc<T> *__restrict__ lats,
+                                                            const int2 *__restrict__ work, int nwork, int nsteps,
+                                                            int parity0, GridBarrier *bar, unsigned int *err,
+                                                            long long timeout_ns, int debug_skip_arrival)
+{
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) s_fail = 0;
+    for (int t = 0; t < nsteps; t++) {
+        const int a = (parity0 + t) & 1;
+        for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+            const int2 it = work[w];
+            const LatDesc<T> &L = lats[it.x];
+            const long long s = (long long)it.y * blockDim.x + threadIdx.x;
+            if (s < L.N) {
+                const Nbr n((int)s, L.nx, L.ny, L.nz);
+                L.phi[s] = phi_site(L.g[a], n, L.S);
+            }
+        }
+        if (debug_skip_arrival && blockIdx.x == 0) return;   // test hook: this CTA never arrives
+        if (!grid_sync(bar, gridDim.x, timeout_ns, err, &s_fail)) return;
+        for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+            const int2 it = work[w];
+            const LatDesc<T> &L = lats[it.x];
+            const long long s = (long long)it.y * blockDim.x + threadIdx.x;
+            if (s < L.N) {
+                const Nbr n((int)s, L.nx, L.ny, L.nz);
+                collide_site<T, SH>(L.f[a], L.g[a], L.phi, const_cast<T *>(L.f[1 - a]),
+                                    const_cast<T *>(L.g[1 - a]), L.p, n, s, L.S);
+            }
+        }
+        if (!grid_sync(bar, gridDim.x, timeout_ns, err, &s_fail)) return;
+    }
+}
+
+}  // namespace
+}  // namespace lbk
+
+struct lb_batch {
+    int n = 0;
+    int precision = LB_FP64;
+    std::vector<lb_ctx *> ctx;
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t stream = nullptr;            // own stream: graphs cannot be captured on the legacy stream
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    void *d_lats = nullptr;
+    int2 *d_work = nullptr;
+    int nwork = 0;
+    lbk::GridBarrier *d_bar = nullptr;
+    unsigned int *d_err = nullptr;
+    int threads = 256;                         // sites per work item = threads per CTA
+    int ctas_per_sm = 0;                       // 0 = as many as fit
+    int grid = 0;
+    int parity = 0;                            // timesteps taken, mod 2
+    long long timeout_ns = 1000000000LL;
+    int debug_skip = 0;
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+void drop_graphs(lb_batch *b)
+{
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+template <typename T, bool SH>
+int batch_tables(lb_batch *b)
+{
+    std::vector<lbk::LatDesc<T>> L(b->n);
+    std::vector<int2> work;
+    for (int k = 0; k < b->n; k++) {
+        lb_ctx *c = b->ctx[k];
+        L[k].nx = c->p.nx;
+        L[k].ny = c->p.ny;
+        L[k].nz = c->p.nz;
+        L[k].N = c->N;
+        L[k].S = c->S;
+        for (int l = 0; l < 2; l++) {
+            L[k].f[l] = (const T *)c->buf.f[l];
+            L[k].g[l] = (const T *)c->buf.g[l];
+        }
+        L[k].phi = (T *)c->phi;
+        L[k].p = lbk::make_coll<T>(c->p);
+        const long long nb = (c->N + b->threads - 1) / b->threads;
+        for (long long j = 0; j < nb; j++) work.push_back(make_int2(k, (int)j));
+    }
+    cudaFree(b->d_lats);
+    cudaFree(b->d_work);
+    b->d_lats = nullptr;
+    b->d_work = nullptr;
+    int rc = lbk::cuda_status(cudaMalloc(&b->d_lats, sizeof(lbk::LatDesc<T>) * b->n));
+    if (!rc) rc = lbk::cuda_status(cudaMalloc(&b->d_work, sizeof(int2) * work.size()));
+    if (!rc) rc = lbk::cuda_status(cudaMemcpy(b->d_lats, L.data(), sizeof(lbk::LatDesc<T>) * b->n,
+                                              cudaMemcpyHostToDevice));
+    if (!rc) rc = lbk::cuda_status(cudaMemcpy(b->d_work, work.data(), sizeof(int2) * work.size(),
+                                              cudaMemcpyHostToDevice));
+    b->nwork = (int)work.size();
+    if (rc) return rc;
+    // co-resident grid
+    int dev = 0, sms = 0, per_sm = 0;
+    rc = lbk::cuda_status(cudaGetDevice(&dev));
+    if (!rc) rc = lbk::cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (!rc) rc = lbk::cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbk::k_batch<T, SH>,
+                                                                                 b->threads, 0));
+    if (rc) return rc;
+    if (per_sm < 1) return LB_ERR_INVALID;
+    const int use = b->ctas_per_sm > 0 && b->ctas_per_sm < per_sm ? b->ctas_per_sm : per_sm;
+    b->grid = use * sms;
+    return LB_OK;
+}
+
+int tables(lb_batch *b)
+{
+    drop_graphs(b);
+    return b->precision == LB_FP64 ? batch_tables<double, false>(b) : batch_tables<float, true>(b);
+}
+
+template <typename T, bool SH>
+int capture(lb_batch *b, int nsteps, int parity, cudaGraphExec_t *out)
+{
+    cudaGraph_t graph = nullptr;
+    int rc = lbk::cuda_status(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    if (rc) return rc;
+    cudaMemsetAsync(b->d_bar, 0, sizeof(lbk::GridBarrier), b->stream);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)b->grid);
+    cfg.blockDim = dim3((unsigned)b->threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = b->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const lbk::LatDesc<T> *lats = (const lbk::LatDesc<T> *)b->d_lats;
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, lbk::k_batch<T, SH>, lats, (const int2 *)b->d_work, b->nwork,
+                                              nsteps, parity, b->d_bar, b->d_err, b->timeout_ns, b->debug_skip);
+    const cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
+    rc = lbk::cuda_status(le != cudaSuccess ? le : ce);
+    if (!rc) rc = lbk::cuda_status(cudaGraphInstantiate(out, graph, 0));
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+}
+
+int batch_sync(lb_batch *b)
+{
+    unsigned int flag = 0;
+    int rc = lbk::cuda_status(cudaMemcpyAsync(&flag, b->d_err, sizeof(flag), cudaMemcpyDeviceToHost, b->stream));
+    if (!rc) rc = lbk::cuda_status(cudaStreamSynchronize(b->stream));
+    if (!rc) rc = lbk::cuda_status(cudaStreamSynchronize(b->user_stream));
+    if (rc) return rc;
+    if (flag) {
+        rc = lbk::cuda_status(cudaMemsetAsync(b->d_err, 0, sizeof(unsigned int), b->stream));
+        if (!rc) rc = lbk::cuda_status(cudaStreamSynchronize(b->stream));
+        return rc ? rc : LB_ERR_TIMEOUT;
+    }
+    return LB_OK;
+}
+
+bool index_ok(const lb_batch *b, int k) { return b && k >= 0 && k < b->n; }
+
+}  // namespace
+
+extern "C" {
+
+void lb_batch_destroy(lb_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    for (lb_ctx *c : b->ctx) {
+        lbk::release_from_batch(c);
+        lb_destroy(c);
+    }
+    cudaFree(b->d_lats);
+    cudaFree(b->d_work);
+    cudaFree(b->d_bar);
+    cudaFree(b->d_err);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    cudaGetLastError();
+    delete b;
+}
+
+int lb_batch_create(int n, const lb_params *p, void *cuda_stream, lb_batch **out)
+{
+    if (!out) return LB_ERR_INVALID;
+    *out = nullptr;
+    if (n < 1 || !p) return LB_ERR_INVALID;
+    for (int k = 1; k < n; k++)
+        if (p[k].precision != p[0].precision) return LB_ERR_INVALID;
+    lb_batch *b = new (std::nothrow) lb_batch();
+    if (!b) return LB_ERR_NOMEM;
+    b->n = n;
+    b->precision = p[0].precision;
+    b->user_stream = (cudaStream_t)cuda_stream;
+    int rc = LB_OK;
+    for (int k = 0; k < n && !rc; k++) {
+        lb_ctx *c = nullptr;
+        rc = lb_create(&p[k], cuda_stream, &c);
+        if (!rc) b->ctx.push_back(c);
+    }
+    if (!rc) rc = lbk::cuda_status(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    if (!rc) rc = lbk::cuda_status(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
+    if (!rc) rc = lbk::cuda_status(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
+    if (!rc) rc = lbk::cuda_status(cudaMalloc(&b->d_bar, sizeof(lbk::GridBarrier)));
+    if (!rc) rc = lbk::cuda_status(cudaMalloc(&b->d_err, sizeof(unsigned int)));
+    if (!rc) rc = lbk::cuda_status(cudaMemset(b->d_err, 0, sizeof(unsigned int)));
+    if (!rc)
+        for (lb_ctx *c : b->ctx) lbk::adopt_into_batch(c, b->d_err);
+    if (!rc) rc = tables(b);
+    if (rc) {
+        lb_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return LB_OK;
+}
+
+int lb_batch_size(const lb_batch *b, int *n, int *work_items, int *grid, int *threads)
+{
+    if (!b) return LB_ERR_INVALID;
+    if (n) *n = b->n;
+    if (work_items) *work_items = b->nwork;
+    if (grid) *grid = b->grid;
+    if (threads) *threads = b->threads;
+    return LB_OK;
+}
+
+int lb_batch_set_launch(lb_batch *b, int threads, int ctas_per_sm)
+{
+    const int maxt = b && b->precision == LB_FP64 ? lbk::kBatchMaxThreads64 : lbk::kBatchMaxThreads;
+    if (!b || threads < 32 || threads > maxt || threads % 32 != 0 || ctas_per_sm < 0) return LB_ERR_INVALID;
+    const int old_t = b->threads, old_c = b->ctas_per_sm;
+    b->threads = threads;
+    b->ctas_per_sm = ctas_per_sm;
+    const int rc = tables(b);
+    if (rc) {
+        b->threads = old_t;
+        b->ctas_per_sm = old_c;
+        tables(b);
+    }
+    return rc;
+}
+
+int lb_batch_set_wait_timeout(lb_batch *b, long long timeout_ns)
+{
+    if (!b || timeout_ns < 1000 || timeout_ns > 60000000000LL) return LB_ERR_INVALID;
+    b->timeout_ns = timeout_ns;
+    drop_graphs(b);
+    return LB_OK;
+}
+
+int lb_batch_debug_skip_arrival(lb_batch *b, int enable)
+{
+    if (!b) return LB_ERR_INVALID;
+    b->debug_skip = enable ? 1 : 0;
+    drop_graphs(b);
+    return LB_OK;
+}
+
+lb_ctx *lb_batch_lattice(lb_batch *b, int k) { return index_ok(b, k) ? b->ctx[k] : nullptr; }
+
+int lb_batch_run(lb_batch *b, int nsteps)
+{
+    if (!b || nsteps < 0) return LB_ERR_INVALID;
+    if (nsteps == 0) return LB_OK;
+    const auto key = std::make_pair(nsteps, b->parity);
+    auto it = b->graphs.find(key);
+    if (it == b->graphs.end()) {
+        cudaGraphExec_t exec = nullptr;
+        const int rc = b->precision == LB_FP64 ? capture<double, false>(b, nsteps, b->parity, &exec)
+                                               : capture<float, true>(b, nsteps, b->parity, &exec);
+        if (rc) return rc;
+        it = b->graphs.emplace(key, exec).first;
+    }
+    int rc = lbk::cuda_status(cudaEventRecord(b->ev_in, b->user_stream));
+    if (!rc) rc = lbk::cuda_status(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+    if (!rc) rc = lbk::cuda_status(cudaGraphLaunch(it->second, b->stream));
+    if (!rc) rc = lbk::cuda_status(cudaEventRecord(b->ev_out, b->stream));
+    if (!rc) rc = lbk::cuda_status(cudaStreamWaitEvent(b->user_stream, b->ev_out, 0));
+    if (rc) return rc;
+    b->parity ^= (nsteps & 1);
+    for (lb_ctx *c : b->ctx) c->buf.cur = b->parity;
+    return LB_OK;
+}
+
+int lb_batch_sync(lb_batch *b)
+{
+    if (!b) return LB_ERR_INVALID;
+    return batch_sync(b);
+}
+
+}  // extern "C"

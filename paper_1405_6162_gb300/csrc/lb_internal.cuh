@@ -43,6 +43,7 @@ struct lb_ctx {
     unsigned int *err_flag = nullptr;         // set by a device-side wait that timed out
     unsigned long long lag_target_skew = 0;   // test hook: makes the waits unsatisfiable
     long long wait_timeout_ns = 1000000000LL; // bound of every device-side wait
+    int batch_owned = 0;                      // member of an lb_batch: stepped and freed by it
     int kernel = LB_KERNEL_AUTO;
     int block_x = 0, block_y = 0, z_chunk = 0;
     lb_alloc_fn alloc = nullptr;
@@ -81,6 +82,10 @@ inline Coll<T> make_coll(const lb_params &p)
     c.g1t = T(og / 6.0); c.g2t = T(og / 12.0);
     return c;
 }
+
+// ensemble membership (lb_api.cu): the member shares the batch's error flag
+void adopt_into_batch(lb_ctx *c, unsigned int *shared_err);
+void release_from_batch(lb_ctx *c);
 
 // status helpers (lb_api.cu)
 int cuda_status(cudaError_t e);

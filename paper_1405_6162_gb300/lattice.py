@@ -113,6 +113,20 @@ class Lattice:
         self._fin = weakref.finalize(self, _destroy, h)
 
     @classmethod
+    def _member(cls, handle, dims, params, precision, owner):
+        """A non-owning view of an ensemble member (freed by its ensemble)."""
+        self = cls.__new__(cls)
+        self.dims = tuple(int(d) for d in dims)
+        self.N = self.dims[0] * self.dims[1] * self.dims[2]
+        self.precision = precision
+        self.params = {k: params[k] for k in ("tau", "tau_g", "rho0", "gamma", "A", "B", "kappa")}
+        self.stream = owner.stream
+        self._h = ctypes.c_void_p(handle)
+        self._owner = owner
+        self._fin = weakref.finalize(self, lambda: None)
+        return self
+
+    @classmethod
     def from_params(cls, dims, params, **kw):
         return cls(*dims, **{k: params[k] for k in ("tau", "tau_g", "rho0", "gamma", "A", "B", "kappa")}, **kw)
 

@@ -97,3 +97,62 @@ def autotune(dims, precision, params, phi0, configs=None, steps=5, save=True, lo
         with open(CACHE, "w") as fh:
             json.dump(db, fh, indent=1)
     return best[0], table
+
+
+def _batch_key(batch) -> str:
+    import hashlib
+    h = hashlib.sha256(repr([sorted(d.items()) for d in batch.specs]).encode()).hexdigest()[:12]
+    return f"{_gpu_name()}|batch{len(batch)}:{h}|{batch.precision}"
+
+
+def batch_candidates(precision):
+    threads = (128, 256) if precision == "fp64" else (128, 256, 512)
+    return [(t, c) for t in threads for c in (0, 1, 2, 3)]
+
+
+def autotune_batch(batch, steps=20, candidates=None, save=True, log=None):
+    """Time every (threads, ctas_per_sm) launch shape of an initialised
+    ensemble for ``steps`` steps, keep the fastest on the ensemble and in the
+    on-disk cache; returns (best, table).  Running the ensemble advances its
+    lattices: re-initialise them afterwards if their state matters."""
+    import torch
+    table = []
+    for t, c in candidates or batch_candidates(batch.precision):
+        try:
+            batch.set_launch(t, c)
+        except Exception as exc:
+            if log:
+                log(f"skip {(t, c)}: {exc}")
+            continue
+        info = batch.info()
+        if c and info[2] == table[-1][2] if table else False:
+            continue
+        batch.run(steps)                   # warm-up (captures the graph)
+        torch.cuda.synchronize()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        batch.run(steps)
+        e.record()
+        e.synchronize()
+        dt = s.elapsed_time(e) / 1e3 / steps
+        table.append(((t, c), dt, info[2]))
+        if log:
+            log(f"threads={t} ctas/SM={c} grid={info[2]}: {dt * 1e3:.3f} ms/step")
+    best = min(table, key=lambda r: r[1])
+    batch.set_launch(*best[0])
+    batch.sync()
+    if save:
+        db = _load()
+        db[_batch_key(batch)] = {"config": list(best[0]), "seconds_per_step": best[1],
+                                 "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        with open(CACHE, "w") as fh:
+            json.dump(db, fh, indent=1)
+    return best[0], [(r[0], r[1]) for r in table]
+
+
+def batch_config(batch):
+    """Cached launch shape of this ensemble, or None."""
+    hit = _load().get(_batch_key(batch))
+    return tuple(hit["config"]) if hit else None

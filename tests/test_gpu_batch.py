@@ -1,0 +1,152 @@
+"""The ensemble path: many uneven lattices in one persistent, graph-captured
+launch, each checked against the CPU oracle run on that lattice alone."""
+import numpy as np
+import pytest
+
+import lb_inputs as L
+import oracle
+from tests.parity import P0, TOL_FP64, rel, u_scale
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    import paper_1405_6162_gb300 as lbpkg
+    lbpkg.build()
+    oracle.build()
+
+
+def _small_ensemble(seed, n=6):
+    specs = L.ensemble(seed, n, lo=3, hi=20)
+    specs[0].update(nx=1, ny=1, nz=7)          # degenerate extents too
+    specs[1].update(nx=13, ny=1, nz=2)
+    return specs
+
+
+def _oracle(spec, phi0, nsteps):
+    dims = (spec["nx"], spec["ny"], spec["nz"])
+    f, g = oracle.step(dims, spec, *oracle.init(dims, spec, phi0), nsteps)
+    return oracle.moments(dims, f, g), u_scale(f)
+
+
+def _phi0(spec, k, amp=0.3):
+    return L.spinodal_phi0(spec["nx"], spec["ny"], spec["nz"], seed=100 + k, amp=amp)
+
+
+TOL_FP32_PER_STEP = {"rho": 2.5e-8, "u": 2.5e-8, "phi": 1e-7}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_shifted"])
+@pytest.mark.parametrize("launch", [(256, 0), (128, 1), (64, 2)])
+def test_ensemble_matches_oracle_per_lattice(precision, launch):
+    from paper_1405_6162_gb300 import Batch
+    specs = _small_ensemble(7)
+    nsteps = 15
+    with Batch(specs, precision=precision) as b:
+        b.set_launch(*launch)
+        for k, d in enumerate(specs):
+            b[k].init(_phi0(d, k))
+        b.run(nsteps)
+        b.sync()
+        for k, d in enumerate(specs):
+            (rho, u, phi), us = _oracle(d, _phi0(d, k), nsteps)
+            got = b[k].moments()
+            for name, a, ref in zip(("rho", "u", "phi"), got, (rho, u, phi)):
+                e = rel(a, ref, us if name == "u" else None)
+                tol = TOL_FP64 if precision == "fp64" else TOL_FP32_PER_STEP[name] * nsteps
+                assert e <= tol, (k, name, e)
+
+
+def test_split_runs_equal_one_run():
+    """Graph per (steps, parity): 7 + 8 steps give exactly the 15-step state."""
+    from paper_1405_6162_gb300 import Batch
+    specs = _small_ensemble(8)
+    out = []
+    for plan in ((15,), (7, 8), (1, 1, 13)):
+        with Batch(specs, precision="fp32_shifted") as b:
+            for k, d in enumerate(specs):
+                b[k].init(_phi0(d, k))
+            for n in plan:
+                b.run(n)
+            out.append([b[k].get_state() for k in range(len(specs))])
+    for other in out[1:]:
+        for (f0, g0), (f1, g1) in zip(out[0], other):
+            assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+
+
+def test_members_belong_to_the_ensemble():
+    from paper_1405_6162_gb300 import Batch, LBError
+    from paper_1405_6162_gb300 import _lib as LL
+    specs = _small_ensemble(9, n=2)
+    with Batch(specs, precision="fp64") as b:
+        h = b[0].handle
+        assert LL.lib().lb_step(h, 1) == LL.LB_ERR_INVALID
+        LL.lib().lb_destroy(h)                  # ignored: the ensemble owns it
+        b[0].init(_phi0(specs[0], 0))
+        b.run(2)
+        b.sync()
+        assert np.isfinite(b[0].reduce()).all()
+        assert LL.lib().lb_batch_lattice(b.handle, 2) is None
+        with pytest.raises(LBError):
+            b.set_launch(48, 0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_shifted"])
+def test_grid_barrier_timeout_is_reported_and_recoverable(precision):
+    """One CTA leaves before the first grid barrier (test hook): every other
+    CTA's bounded wait gives up, the kernel ends, the host sees
+    LB_ERR_TIMEOUT, and after re-initialisation the ensemble is exact."""
+    from paper_1405_6162_gb300 import Batch, LBError
+    from paper_1405_6162_gb300 import _lib as LL
+    specs = _small_ensemble(10, n=3)
+    with Batch(specs, precision=precision) as b:
+        b.set_wait_timeout(0.05)
+        LL.check(LL.lib().lb_batch_debug_skip_arrival(b.handle, 1), "hook")
+        for k, d in enumerate(specs):
+            b[k].init(_phi0(d, k))
+        b.run(3)
+        with pytest.raises(LBError) as ei:
+            b.sync()
+        assert ei.value.code == LL.LB_ERR_TIMEOUT
+        b.sync()
+        LL.check(LL.lib().lb_batch_debug_skip_arrival(b.handle, 0), "hook")
+        for k, d in enumerate(specs):
+            b[k].init(_phi0(d, k))
+        b.run(4)
+        b.sync()
+        for k, d in enumerate(specs):
+            (rho, u, phi), us = _oracle(d, _phi0(d, k), 4)
+            got = b[k].moments()
+            tol = TOL_FP64 if precision == "fp64" else 1e-6
+            assert rel(got[2], phi) <= tol
+
+
+def test_ensemble_64_uneven_lattices_500_steps_fp32():
+    """The 64-lattice workload: sides U{16..64}, tau ~ U[0.55, 1.5],
+    kappa ~ U[0.01, 0.08], FP32-shifted, 500 steps in one graph replay.
+    Every lattice conserves mass and phi (FP64 sums); the three smallest are
+    compared with the oracle."""
+    from paper_1405_6162_gb300 import Batch
+    specs = L.ensemble(3, 64)
+    nsteps = 500
+    phis = [L.spinodal_phi0(d["nx"], d["ny"], d["nz"], seed=1000 + k) for k, d in enumerate(specs)]
+    with Batch(specs, precision="fp32_shifted") as b:
+        for k in range(len(specs)):
+            b[k].init(phis[k])
+        r0 = [b[k].reduce() for k in range(len(specs))]
+        b.run(nsteps)
+        b.sync()
+        r1 = [b[k].reduce() for k in range(len(specs))]
+        for k, d in enumerate(specs):
+            n = d["nx"] * d["ny"] * d["nz"]
+            assert abs(r1[k][0] - r0[k][0]) <= 1e-6 * n, (k, r1[k][0] - r0[k][0])
+            assert abs(r1[k][4] - r0[k][4]) <= 1e-6 * n, (k, r1[k][4] - r0[k][4])
+        order = sorted(range(len(specs)), key=lambda k: specs[k]["nx"] * specs[k]["ny"] * specs[k]["nz"])
+        for k in order[:3]:
+            (rho, u, phi), us = _oracle(specs[k], phis[k], nsteps)
+            got = b[k].moments()
+            errs = {name: rel(a, ref, us if name == "u" else None)
+                    for name, a, ref in zip(("rho", "u", "phi"), got, (rho, u, phi))}
+            print("lattice", k, specs[k]["nx"], specs[k]["ny"], specs[k]["nz"], errs)
+            assert errs["rho"] <= 1e-5 and errs["u"] <= 1e-5 and errs["phi"] <= 1e-3, errs
