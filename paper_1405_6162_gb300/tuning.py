@@ -117,6 +117,7 @@ def autotune_batch(batch, steps=20, candidates=None, save=True, log=None):
     lattices: re-initialise them afterwards if their state matters."""
     import torch
     table = []
+    seen = set()
     for t, c in candidates or batch_candidates(batch.precision):
         try:
             batch.set_launch(t, c)
@@ -125,8 +126,9 @@ def autotune_batch(batch, steps=20, candidates=None, save=True, log=None):
                 log(f"skip {(t, c)}: {exc}")
             continue
         info = batch.info()
-        if c and info[2] == table[-1][2] if table else False:
+        if (t, info[2]) in seen:          # same grid as a shape already timed
             continue
+        seen.add((t, info[2]))
         batch.run(steps)                   # warm-up (captures the graph)
         torch.cuda.synchronize()
         s = torch.cuda.Event(enable_timing=True)
