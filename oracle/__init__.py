@@ -76,7 +76,9 @@ def _arr(a, kind):
 
 
 def _prm(params, kind):
-    return _arr(np.array([params[k] for k in PARAM_ORDER]), kind)
+    vals = [params[k] for k in PARAM_ORDER]
+    dt = np.complex128 if kind == "complex" else np.float64
+    return _arr(np.array(vals, dtype=dt), kind)
 
 
 def velocity_set():
@@ -177,3 +179,66 @@ def reduce(dims, f, g, kind="serial"):
     out = np.zeros(5, dtype=_dtype(kind))
     _lib(kind).orc_reduce(nx, ny, nz, fp, gp, out.ctypes.data_as(ctypes.c_void_p))
     return out
+
+
+def step_adjoint(dims, params, f, g, af, ag):
+    """One reverse step: given F(t) = (f, g) and F_bar(t+1) = (af, ag),
+    returns (F_bar(t) f-part, g-part, dJ/dkappa of this step)."""
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    prm, pp = _prm(params, "serial")
+    f, fp = _arr(np.reshape(f, -1), "serial")
+    g, gp = _arr(np.reshape(g, -1), "serial")
+    af = np.array(af, dtype=np.float64, copy=True).reshape(-1)
+    ag = np.array(ag, dtype=np.float64, copy=True).reshape(-1)
+    dk = np.zeros(1)
+    _lib().orc_step_adjoint(nx, ny, nz, pp, fp, gp, af.ctypes.data_as(ctypes.c_void_p),
+                            ag.ctypes.data_as(ctypes.c_void_p), dk.ctypes.data_as(ctypes.c_void_p))
+    return af.reshape(19, n), ag.reshape(19, n), float(dk[0])
+
+
+def init_adjoint(dims, params, phi0, af0, ag0, u0=None):
+    """Reverse of the initialisation: (dJ/dphi0 [N], dJ/dkappa of init)."""
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    prm, pp = _prm(params, "serial")
+    phi0, php = _arr(phi0, "serial")
+    up = None
+    if u0 is not None:
+        u0, up = _arr(np.reshape(u0, (3 * n,)), "serial")
+    af0, ap = _arr(np.reshape(af0, -1), "serial")
+    ag0, gp = _arr(np.reshape(ag0, -1), "serial")
+    out = np.zeros(n)
+    dk = np.zeros(1)
+    _lib().orc_init_adjoint(nx, ny, nz, pp, php, up, ap, gp, out.ctypes.data_as(ctypes.c_void_p),
+                            dk.ctypes.data_as(ctypes.c_void_p))
+    return out, float(dk[0])
+
+
+def trajectory_gradient(dims, params, phi0, phi_target, nsteps):
+    """J = sum_x (phi_T - phi_target)^2 after ``nsteps`` from the equilibrium
+    start, and (dJ/dphi0, dJ/dkappa) by the reverse sweep (all states kept:
+    small lattices only)."""
+    f, g = init(dims, params, phi0)
+    states = [(f, g)]
+    for _ in range(nsteps):
+        f, g = step(dims, params, f, g, 1)
+        states.append((f, g))
+    phi_t = g.sum(0)
+    J = float(np.sum((phi_t - phi_target) ** 2))
+    af = np.zeros_like(f)
+    ag = np.tile(2.0 * (phi_t - phi_target), (19, 1))
+    dk = 0.0
+    for t in range(nsteps - 1, -1, -1):
+        af, ag, d = step_adjoint(dims, params, *states[t], af, ag)
+        dk += d
+    phi_bar, d = init_adjoint(dims, params, phi0, af, ag)
+    return J, phi_bar, dk + d
+
+
+def trajectory_loss(dims, params, phi0, phi_target, nsteps, kind="serial"):
+    """J alone (any build; complex inputs give the complex-step derivative)."""
+    f, g = init(dims, params, phi0, kind=kind)
+    f, g = step(dims, params, f, g, nsteps, kind=kind)
+    phi_t = g.sum(0)
+    return np.sum((phi_t - phi_target) ** 2)

@@ -261,3 +261,216 @@ void orc_reduce(int nx, int ny, int nz, const real *f, const real *g, real *out)
             out[4] += g[i * N + s];
         }
 }
+
+#ifndef ORC_COMPLEX
+/* ------------------------------------------------------------------------
+ * Reverse mode (adjoint) of the timestep and of the initialisation, FP64.
+ *
+ * State F(t) = (f, g)(x, t) after streaming.  Adjoint F_bar(t) = dJ/dF(t).
+ * One reverse step, given F(t) and F_bar(t+1):
+ *   1. streaming transposed: fs_bar_i(x) = f_bar_i(x + c_i, t+1) (g alike);
+ *   2. per site, the collision's vector-Jacobian product, which yields
+ *      f_bar(x, t), the direct part of g_bar, and the adjoints of phi, of the
+ *      gradient d_a phi and of lap phi at x, plus dJ/dkappa;
+ *   3. the stencils transposed: phi_bar(x) gathers
+ *      (d_bar_a(x - e_a) - d_bar_a(x + e_a))/2 and
+ *      sum_a (l_bar(x - e_a) + l_bar(x + e_a)) - 6 l_bar(x);
+ *   4. phi = sum g transposed: g_bar_i(x, t) += phi_bar(x).
+ * The collision's forward quantities are recomputed from F(t).
+ * ---------------------------------------------------------------------- */
+
+/* Adjoint of the equilibrium map at one site.  Given weights fe_bar[i] on
+ * feq_i and ge_bar[i] on geq_i, accumulate the adjoints of rho, j, phi, the
+ * gradient d, lap, and kappa.  ``with_flow`` = 0 treats rho and j as
+ * constants (the initial state, where they are inputs). */
+static void equilibrium_vjp(const double *prm, double rho, const double *j, double phi,
+                            const double *d, double lap, const double *fe_bar, const double *ge_bar,
+                            int with_flow, double *rho_bar, double *j_bar, double *phi_bar,
+                            double *d_bar, double *lap_bar, double *kappa_bar)
+{
+    const double cs2 = 1.0 / 3.0;
+    double A = prm[P_A], B = prm[P_B], kappa = prm[P_KAPPA], gam = prm[P_GAMMA];
+    double u[3];
+    for (int a = 0; a < 3; a++) u[a] = j[a] / rho;
+    /* feq_i = w_i [rho + c.j/cs2 + (c S c - cs2 tr S)/(2 cs2^2)]
+     * geq_i = w_i [phi + phi c.u/cs2 + (c G c - cs2 tr G)/(2 cs2^2)] */
+    double Sb[3][3] = {{0}}, Gb[3][3] = {{0}};
+    double u_bar[3] = {0, 0, 0};
+    for (int i = 0; i < NV; i++) {
+        double cu = 0.0;
+        for (int a = 0; a < 3; a++) cu += cv[i][a] * u[a];
+        double wf = wv[i] * fe_bar[i], wg = wv[i] * ge_bar[i];
+        *rho_bar += wf;
+        for (int a = 0; a < 3; a++) {
+            j_bar[a] += wf * cv[i][a] / cs2;
+            u_bar[a] += wg * phi * cv[i][a] / cs2;
+        }
+        *phi_bar += wg * (1.0 + cu / cs2);
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) {
+                double Q = cv[i][a] * cv[i][b] - (a == b ? cs2 : 0.0);
+                Sb[a][b] += wf * Q / (2.0 * cs2 * cs2);
+                Gb[a][b] += wg * Q / (2.0 * cs2 * cs2);
+            }
+    }
+    /* G = (Gamma mu - phi cs2) I + phi u u */
+    double trG = Gb[0][0] + Gb[1][1] + Gb[2][2];
+    double mu_bar = gam * trG;
+    *phi_bar += -cs2 * trG;
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            *phi_bar += Gb[a][b] * u[a] * u[b];
+            u_bar[a] += Gb[a][b] * phi * u[b];
+            u_bar[b] += Gb[a][b] * phi * u[a];
+        }
+    /* S = pb I + kappa d d + rho u u, with rho u u = j j / rho */
+    double pb_bar = Sb[0][0] + Sb[1][1] + Sb[2][2];
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            d_bar[a] += Sb[a][b] * kappa * d[b];
+            d_bar[b] += Sb[a][b] * kappa * d[a];
+            *kappa_bar += Sb[a][b] * d[a] * d[b];
+            if (with_flow) {
+                j_bar[a] += Sb[a][b] * j[b] / rho;
+                j_bar[b] += Sb[a][b] * j[a] / rho;
+                *rho_bar -= Sb[a][b] * j[a] * j[b] / (rho * rho);
+            }
+        }
+    /* pb = A/2 phi^2 + 3B/4 phi^4 - kappa phi lap - kappa/2 |d|^2 */
+    double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    *phi_bar += pb_bar * (A * phi + 3.0 * B * phi * phi * phi - kappa * lap);
+    *lap_bar += -kappa * phi * pb_bar;
+    for (int a = 0; a < 3; a++) d_bar[a] += -kappa * d[a] * pb_bar;
+    *kappa_bar += pb_bar * (-phi * lap - 0.5 * dd);
+    /* mu = A phi + B phi^3 - kappa lap */
+    *phi_bar += mu_bar * (A + 3.0 * B * phi * phi);
+    *lap_bar += -kappa * mu_bar;
+    *kappa_bar += -lap * mu_bar;
+    /* u = j / rho */
+    if (with_flow) {
+        for (int a = 0; a < 3; a++) {
+            j_bar[a] += u_bar[a] / rho;
+            *rho_bar -= u_bar[a] * j[a] / (rho * rho);
+        }
+    }
+}
+
+/* phi_bar(x) += transposed 7-point stencils of (d_bar, lap_bar). */
+static void stencil_transpose(int nx, int ny, int nz, const double *d_bar, const double *lap_bar,
+                              double *phi_bar)
+{
+    long N = (long)nx * ny * nz;
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                long s = site(x, y, z, nx, ny, nz);
+                long xp = site(x + 1, y, z, nx, ny, nz), xm = site(x - 1, y, z, nx, ny, nz);
+                long yp = site(x, y + 1, z, nx, ny, nz), ym = site(x, y - 1, z, nx, ny, nz);
+                long zp = site(x, y, z + 1, nx, ny, nz), zm = site(x, y, z - 1, nx, ny, nz);
+                phi_bar[s] += (d_bar[0 * N + xm] - d_bar[0 * N + xp]) / 2.0
+                            + (d_bar[1 * N + ym] - d_bar[1 * N + yp]) / 2.0
+                            + (d_bar[2 * N + zm] - d_bar[2 * N + zp]) / 2.0
+                            + lap_bar[xm] + lap_bar[xp] + lap_bar[ym] + lap_bar[yp]
+                            + lap_bar[zm] + lap_bar[zp] - 6.0 * lap_bar[s];
+            }
+}
+
+/* One reverse step: (f, g) = F(t); (af, ag) holds F_bar(t+1) on entry and
+ * F_bar(t) on return; *dkappa accumulates dJ/dkappa of this step. */
+void orc_step_adjoint(int nx, int ny, int nz, const double *prm, const double *f, const double *g,
+                      double *af, double *ag, double *dkappa)
+{
+    velocity_set();
+    long N = (long)nx * ny * nz;
+    double *phi = malloc(sizeof(double) * N), *grad = malloc(sizeof(double) * 3 * N);
+    double *lap = malloc(sizeof(double) * N);
+    double *fs_bar = malloc(sizeof(double) * NV * N), *gs_bar = malloc(sizeof(double) * NV * N);
+    double *phi_bar = calloc(N, sizeof(double)), *d_bar = calloc(3 * N, sizeof(double));
+    double *lap_bar = calloc(N, sizeof(double));
+    double omega = 1.0 / prm[P_TAU], omega_g = 1.0 / prm[P_TAUG];
+    for (long s = 0; s < N; s++) {
+        double acc = 0.0;
+        for (int i = 0; i < NV; i++) acc += g[i * N + s];
+        phi[s] = acc;
+    }
+    orc_gradients(nx, ny, nz, phi, grad, lap);
+    /* 1. streaming transposed */
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                long s = site(x, y, z, nx, ny, nz);
+                for (int i = 0; i < NV; i++) {
+                    long dst = site(x + cv[i][0], y + cv[i][1], z + cv[i][2], nx, ny, nz);
+                    fs_bar[i * N + s] = af[i * N + dst];
+                    gs_bar[i * N + s] = ag[i * N + dst];
+                }
+            }
+    /* 2. collision, transposed per site */
+    double kap = 0.0;
+    for (long s = 0; s < N; s++) {
+        double rho = 0.0, j[3] = {0, 0, 0}, d[3], fe_bar[NV], ge_bar[NV];
+        for (int i = 0; i < NV; i++) {
+            rho += f[i * N + s];
+            for (int a = 0; a < 3; a++) j[a] += f[i * N + s] * cv[i][a];
+        }
+        for (int a = 0; a < 3; a++) d[a] = grad[a * N + s];
+        for (int i = 0; i < NV; i++) {
+            fe_bar[i] = omega * fs_bar[i * N + s];
+            ge_bar[i] = omega_g * gs_bar[i * N + s];
+        }
+        double rho_bar = 0.0, j_bar[3] = {0, 0, 0}, pb = 0.0, db[3] = {0, 0, 0}, lb = 0.0;
+        equilibrium_vjp(prm, rho, j, phi[s], d, lap[s], fe_bar, ge_bar, 1, &rho_bar, j_bar, &pb, db, &lb,
+                        &kap);
+        phi_bar[s] += pb;
+        for (int a = 0; a < 3; a++) d_bar[a * N + s] = db[a];
+        lap_bar[s] = lb;
+        for (int i = 0; i < NV; i++) {
+            double jc = 0.0;
+            for (int a = 0; a < 3; a++) jc += j_bar[a] * cv[i][a];
+            af[i * N + s] = (1.0 - omega) * fs_bar[i * N + s] + rho_bar + jc;
+            ag[i * N + s] = (1.0 - omega_g) * gs_bar[i * N + s];
+        }
+    }
+    /* 3. stencils transposed; 4. phi = sum g transposed */
+    stencil_transpose(nx, ny, nz, d_bar, lap_bar, phi_bar);
+    for (long s = 0; s < N; s++)
+        for (int i = 0; i < NV; i++) ag[i * N + s] += phi_bar[s];
+    *dkappa += kap;
+    free(phi); free(grad); free(lap); free(fs_bar); free(gs_bar);
+    free(phi_bar); free(d_bar); free(lap_bar);
+}
+
+/* Reverse of the initialisation F(0) = equilibria(rho0, rho0 u0, phi0):
+ * given F_bar(0) = (af, ag), phi0_bar receives dJ/dphi0 (overwritten) and
+ * *dkappa accumulates the initialisation's part of dJ/dkappa. */
+void orc_init_adjoint(int nx, int ny, int nz, const double *prm, const double *phi0, const double *u0,
+                      const double *af, const double *ag, double *phi0_bar, double *dkappa)
+{
+    velocity_set();
+    long N = (long)nx * ny * nz;
+    double *grad = malloc(sizeof(double) * 3 * N), *lap = malloc(sizeof(double) * N);
+    double *d_bar = calloc(3 * N, sizeof(double)), *lap_bar = calloc(N, sizeof(double));
+    orc_gradients(nx, ny, nz, phi0, grad, lap);
+    double rho = prm[P_RHO0], kap = 0.0;
+    for (long s = 0; s < N; s++) {
+        double j[3], d[3], fe_bar[NV], ge_bar[NV];
+        for (int a = 0; a < 3; a++) {
+            j[a] = u0 ? rho * u0[a * N + s] : 0.0;
+            d[a] = grad[a * N + s];
+        }
+        for (int i = 0; i < NV; i++) {
+            fe_bar[i] = af[i * N + s];
+            ge_bar[i] = ag[i * N + s];
+        }
+        double rho_bar = 0.0, j_bar[3] = {0, 0, 0}, pb = 0.0, db[3] = {0, 0, 0}, lb = 0.0;
+        equilibrium_vjp(prm, rho, j, phi0[s], d, lap[s], fe_bar, ge_bar, 0, &rho_bar, j_bar, &pb, db, &lb,
+                        &kap);
+        phi0_bar[s] = pb;
+        for (int a = 0; a < 3; a++) d_bar[a * N + s] = db[a];
+        lap_bar[s] = lb;
+    }
+    stencil_transpose(nx, ny, nz, d_bar, lap_bar, phi0_bar);
+    *dkappa += kap;
+    free(grad); free(lap); free(d_bar); free(lap_bar);
+}
+#endif /* ORC_COMPLEX */
