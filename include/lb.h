@@ -226,6 +226,29 @@ int lb_debug_wait_skew(lb_ctx *c, unsigned long long skew);
 int lb_step_fp64_noalloc(const lb_params *p, const double *fa, const double *ga, double *fb, double *gb,
                          void *cuda_stream);
 
+/* ---- Reverse mode (adjoint) of the FP64 timestep ----
+ * For gradients of a loss on the state at time T with respect to the
+ * initial order parameter and kappa (back-propagation through time).
+ * States and adjoints use the ABI convention: device double[19][N] arrays,
+ * post-streaming, ABI velocity order.  Contexts must be LB_FP64.  The adjoint
+ * scratch (6 N doubles) is allocated on first use.  Paper: no counterpart
+ * (the method's own gradients are not in the paper).
+ *
+ * One reverse step: given F(t) = (f, g) and F_bar(t+1) = (af_in, ag_in),
+ * writes F_bar(t) = (af_out, ag_out) (must not alias the inputs) and adds
+ * this step's dJ/dkappa to *dkappa (a device double).  It transposes, in
+ * order, the streaming, the collision (with the stress, mu and u = j/rho
+ * recomputed from F(t)), the 7-point stencils and phi = sum g. */
+int lb_adjoint_step(lb_ctx *c, const double *f, const double *g, const double *af_in, const double *ag_in,
+                    double *af_out, double *ag_out, double *dkappa);
+
+/* Reverse of lb_init: given F_bar(0) = (af0, ag0), writes dJ/dphi0 to
+ * phi0_bar (device double[N]) and adds the initialisation's dJ/dkappa to
+ * *dkappa.  phi0 and u0 (NULL = fluid at rest) are device arrays as in
+ * lb_init. */
+int lb_adjoint_init(lb_ctx *c, const double *phi0, const double *u0, const double *af0, const double *ag0,
+                    double *phi0_bar, double *dkappa);
+
 /* ---- Ensembles: many independent lattices in one persistent launch ----
  * An ensemble holds n lattices of any extents and parameters (one precision
  * for all).  lb_batch_run advances every lattice by nsteps timesteps with

@@ -64,6 +64,8 @@ SIGNATURES = {
     "lb_set_wait_timeout": (_I, [_P, ctypes.c_longlong]),
     "lb_debug_wait_skew": (_I, [_P, ctypes.c_ulonglong]),
     "lb_step_fp64_noalloc": (_I, [ctypes.POINTER(lb_params), _P, _P, _P, _P, _P]),
+    "lb_adjoint_step": (_I, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "lb_adjoint_init": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "lb_batch_create": (_I, [_I, ctypes.POINTER(lb_params), _P, ctypes.POINTER(_P)]),
     "lb_batch_destroy": (None, [_P]),
     "lb_batch_lattice": (_P, [_P, _I]),

@@ -60,6 +60,10 @@ void free_all(lb_ctx *c)
     dev_free(c, c->dev_out, 8 * sizeof(double));
     dev_free(c, c->lag_counters, (size_t)(c->p.nz + 1) * sizeof(unsigned long long));
     if (!c->batch_owned) dev_free(c, c->err_flag, sizeof(unsigned int));
+    dev_free(c, c->adj, 6 * (size_t)c->N * sizeof(double));
+    dev_free(c, c->adj_part, (size_t)lbk::adjoint_blocks(c->N) * sizeof(double));
+    c->adj = nullptr;
+    c->adj_part = nullptr;
     c->lag_counters = nullptr;
     c->err_flag = nullptr;
     c->phi = nullptr;
@@ -231,6 +235,33 @@ void lb_destroy(lb_ctx *c)
     cudaGetLastError();
     free_all(c);
     delete c;
+}
+
+static int ensure_adj(lb_ctx *c)
+{
+    if (!c->adj) c->adj = (double *)dev_alloc(c, 6 * (size_t)c->N * sizeof(double));
+    if (!c->adj_part) c->adj_part = (double *)dev_alloc(c, (size_t)lbk::adjoint_blocks(c->N) * sizeof(double));
+    return c->adj && c->adj_part ? LB_OK : LB_ERR_NOMEM;
+}
+
+int lb_adjoint_step(lb_ctx *c, const double *f, const double *g, const double *af_in, const double *ag_in,
+                    double *af_out, double *ag_out, double *dkappa)
+{
+    if (!c || c->p.precision != LB_FP64 || !f || !g || !af_in || !ag_in || !af_out || !ag_out || !dkappa)
+        return LB_ERR_INVALID;
+    if (af_out == af_in || ag_out == ag_in || af_out == ag_in || ag_out == af_in) return LB_ERR_INVALID;
+    const int rc = ensure_adj(c);
+    if (rc) return rc;
+    return lbk::launch_adjoint_step(c, f, g, af_in, ag_in, af_out, ag_out, dkappa, c->adj, c->adj_part);
+}
+
+int lb_adjoint_init(lb_ctx *c, const double *phi0, const double *u0, const double *af0, const double *ag0,
+                    double *phi0_bar, double *dkappa)
+{
+    if (!c || c->p.precision != LB_FP64 || !phi0 || !af0 || !ag0 || !phi0_bar || !dkappa) return LB_ERR_INVALID;
+    const int rc = ensure_adj(c);
+    if (rc) return rc;
+    return lbk::launch_adjoint_init(c, phi0, u0, af0, ag0, phi0_bar, dkappa, c->adj, c->adj_part);
 }
 
 int lb_sync(lb_ctx *c)

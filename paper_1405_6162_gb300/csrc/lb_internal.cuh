@@ -43,6 +43,8 @@ struct lb_ctx {
     unsigned int *err_flag = nullptr;         // set by a device-side wait that timed out
     unsigned long long lag_target_skew = 0;   // test hook: makes the waits unsatisfiable
     long long wait_timeout_ns = 1000000000LL; // bound of every device-side wait
+    double *adj = nullptr;        // [6N] adjoint scratch (lazy): phi_bar, d_bar (3), lap_bar, phi
+    double *adj_part = nullptr;   // per-CTA partial dJ/dkappa
     int batch_owned = 0;                      // member of an lb_batch: stepped and freed by it
     int kernel = LB_KERNEL_AUTO;
     int block_x = 0, block_y = 0, z_chunk = 0;
@@ -112,6 +114,13 @@ int fused_validate(int precision, int block_x, int block_y, int z_chunk);
 // staged kernel (lb_staged.cu)
 int launch_step_staged(lb_ctx *c, int nsteps);
 int staged_validate(int precision, int block_x, int block_y, int z_chunk);
+
+// adjoint (lb_adjoint.cu)
+int adjoint_blocks(long long N);
+int launch_adjoint_step(lb_ctx *c, const double *f, const double *g, const double *af_in, const double *ag_in,
+                        double *af_out, double *ag_out, double *dkappa, double *aux, double *kpart);
+int launch_adjoint_init(lb_ctx *c, const double *phi0, const double *u0, const double *af0, const double *ag0,
+                        double *phi0_bar, double *dkappa, double *aux, double *kpart);
 
 // lagged kernel (lb_lag.cu)
 int launch_step_lag(lb_ctx *c, int nsteps);
