@@ -40,7 +40,7 @@ def spinodal_reference():
 
 @pytest.mark.parametrize("precision,bounds", [
     ("fp64", {"rho": 1e-11, "u": 1e-11, "phi": 1e-11}),
-    ("fp32_shifted", {"rho": 1e-6, "u": 1e-5, "phi": 1e-2}),
+    ("fp32_shifted", {"rho": 1e-6, "u": 1e-6, "phi": 1e-4}),
 ])
 def test_spinodal_64cubed_1000_steps(spinodal_reference, precision, bounds):
     from paper_1405_6162_gb300 import Lattice
@@ -82,7 +82,12 @@ def test_shear_wave_decay_rate_256cubed(precision, tau):
     rate = -np.polyfit(ts[sel], np.log(np.array(amps))[sel], 1)[0]
     nu = (tau - 0.5) / 3
     print(f"shear wave tau={tau} {precision}: rate {rate:.6e} vs nu k^2 {nu * k * k:.6e}")
-    assert abs(rate / (nu * k * k) - 1) < 1e-3
+    # FP64: the lattice rate equals nu k^2 to O(k^2) (1e-3).  FP32: each step
+    # changes a stored value by a fraction nu k^2 of itself, only ~1/(nu k^2)
+    # ulps, so float rounding bounds the measured rate to ~2^-23 / (nu k^2)
+    # (6e-3 at tau = 0.6, 1.2e-3 at tau = 1)
+    tol = 1e-3 if precision == "fp64" else max(1e-3, 2.0 ** -23 / (nu * k * k))
+    assert abs(rate / (nu * k * k) - 1) < tol
 
 
 def _newton_profile(n, amplitude=1.0):
@@ -100,7 +105,10 @@ def _newton_profile(n, amplitude=1.0):
     return p
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-4), ("fp32_shifted", 1e-4)])
+# the start has uniform density, so the pressure balance across the
+# interfaces is restored by a transient that advects phi by ~1e-4 (both
+# precisions alike) -- still 100x below the continuum profile's deviation
+@pytest.mark.parametrize("precision,tol", [("fp64", 5e-4), ("fp32_shifted", 5e-4)])
 def test_discrete_interface_profile_is_kept_256cubed(precision, tol):
     """Started on the discrete mu = 0 profile (the LB steady state), two flat
     interfaces stay on it; the continuum tanh(x/xi) differs from it by the
