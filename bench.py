@@ -62,10 +62,14 @@ def _peaks():
         return FALLBACK_HBM, "fallback"
 
 
+# sources the default timestep's kernels are compiled from
+STEP_SOURCES = ("d3q19.cuh", "lb_site.cuh", "lb_internal.cuh", "lb_kernels.cu")
+
+
 def _kernel_sha():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1405_6162_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in STEP_SOURCES:
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(name.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -177,6 +181,73 @@ def _oracle_errors(torch, params):
     return errs, base
 
 
+def _ensemble(torch):
+    """The 64-lattice ensemble (sides U{16..64}, per-lattice tau and kappa,
+    FP32-shifted), 500 steps in one graph replay of one persistent launch."""
+    from paper_1405_6162_gb300 import Batch, tuning
+    specs = LI.ensemble(3, 64)
+
+    def init(b):
+        for k, d in enumerate(specs):
+            b[k].init(LI.spinodal_phi0(d["nx"], d["ny"], d["nz"], seed=1000 + k))
+
+    with Batch(specs, precision="fp32_shifted") as b:
+        init(b)
+        cfg = tuning.batch_config(b)
+        if cfg is None:
+            cfg, _ = tuning.autotune_batch(b, steps=10)
+            init(b)
+        b.set_launch(*cfg)
+        b.run(500)                    # captures the graph
+        b.sync()
+        init(b)
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        b.run(500)
+        e.record()
+        e.synchronize()
+        b.sync()
+        t = s.elapsed_time(e) / 1e3
+        info = b.info()
+        return {"lattices": len(specs), "sites": b.sites, "steps": 500, "seconds": t,
+                "MLUPS": b.sites * 500 / t / 1e6, "precision": "fp32_shifted",
+                "launch": {"threads": info[3], "ctas": info[2], "work_items": info[1]},
+                "graph_replays": 1}
+
+
+def _adjoint(torch):
+    """Gradient of sum (phi_T - phi_target)^2 wrt phi0 and kappa, 64^3,
+    T = 200, FP64, sqrt(T) checkpoints; forward-only time for reference."""
+    import time as _t
+    from paper_1405_6162_gb300.adjoint import trajectory
+    dims, T = (64, 64, 64), 200
+    params = dict(LI.DEFAULT_PARAMS)
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    phi0 = cu(LI.spinodal_phi0(*dims, seed=4))
+    xi = LI.interface_width(params["A"], params["kappa"])
+    tgt = cu(LI.droplet_target(*dims, radius=16.0, xi=xi, seed=5))
+    with torch.no_grad():
+        trajectory(phi0, params["kappa"], dims, params, T)       # warm-up
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    with torch.no_grad():
+        trajectory(phi0, params["kappa"], dims, params, T)
+    torch.cuda.synchronize()
+    t_fwd = _t.perf_counter() - t0
+    x = phi0.clone().requires_grad_(True)
+    kap = torch.tensor(params["kappa"], dtype=torch.float64, device="cuda", requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    J = ((trajectory(x, kap, dims, params, T) - tgt) ** 2).sum()
+    J.backward()
+    torch.cuda.synchronize()
+    t_all = _t.perf_counter() - t0
+    return {"lattice": list(dims), "steps": T, "precision": "fp64", "checkpoints": "every 14 steps (~sqrt T)",
+            "forward_s": t_fwd, "forward_backward_s": t_all, "ratio": t_all / t_fwd,
+            "dJ_dkappa": kap.grad.item()}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -252,6 +323,8 @@ def run_ours(args):
            "h2d_bytes_per_step": n * 8 / E2E_STEPS, "d2h_bytes_per_step": n * 8 / E2E_STEPS,
            "steps_per_transfer": E2E_STEPS}
 
+    ens = _ensemble(torch)
+    adj = _adjoint(torch)
     if rank != 0:
         return
     errs, cpu = (None, None)
@@ -303,6 +376,8 @@ def run_ours(args):
         "error_vs_oracle": ({"sample": f"{ORACLE_SAMPLE[0]}^3 spinodal seed 1, {ORACLE_STEPS} steps, "
                                        "max|gpu-oracle| / max|oracle| per field (u: / max sum_i|f_i c_i|/rho)", **errs} if errs else None),
         "clocks": r32["clocks"],
+        "ensemble": ens,
+        "adjoint": adj,
         "e2e": e2e,
         "gpu_launches": args.steps * (2 if r32["cfg"][0] in ("auto", "two_pass") else 1),
         "cpu_baseline": cpu,
