@@ -26,7 +26,16 @@ namespace lbk {
 
 namespace {
 
-constexpr int kBatchMaxThreads = 512;     // FP32 CTA size limit
+#ifndef LBK_BATCH_MAXT32
+#define LBK_BATCH_MAXT32 512
+#endif
+#ifndef LBK_BATCH_MINB32
+#define LBK_BATCH_MINB32 1   // FP32 CTAs per SM the register budget must allow
+#endif
+#ifndef LBK_BATCH_MINB64
+#define LBK_BATCH_MINB64 1
+#endif
+constexpr int kBatchMaxThreads = LBK_BATCH_MAXT32;     // FP32 CTA size limit
 constexpr int kBatchMaxThreads64 = 256;   // FP64: more registers per thread
 
 template <typename T>
@@ -86,7 +95,8 @@ __device__ bool grid_sync(GridBarrier *bar, unsigned int nblocks, long long time
 }
 
 template <typename T, bool SH>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? kBatchMaxThreads64 : kBatchMaxThreads) k_batch(const LatDesc<T> *__restrict__ lats,
+__global__ void __launch_bounds__(sizeof(T) == 8 ? kBatchMaxThreads64 : kBatchMaxThreads,
+                                  sizeof(T) == 8 ? LBK_BATCH_MINB64 : LBK_BATCH_MINB32) k_batch(const LatDesc<T> *__restrict__ lats,
                                                             const int2 *__restrict__ work, int nwork, int nsteps,
                                                             int parity0, GridBarrier *bar, unsigned int *err,
                                                             long long timeout_ns, int debug_skip_arrival)

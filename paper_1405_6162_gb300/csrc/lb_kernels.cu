@@ -56,8 +56,15 @@ __global__ void __launch_bounds__(256) k_phi_pull(const T *__restrict__ ga, T *_
     phi[s] = phi_site(ga, n, S);
 }
 
+#ifndef LBK_K2_MINB64
+#define LBK_K2_MINB64 1   // FP64 collide/stream: CTAs per SM the register budget must allow
+#endif
+#ifndef LBK_K2_MINB32
+#define LBK_K2_MINB32 1
+#endif
+
 template <typename T, bool SH>
-__global__ void __launch_bounds__(256) k_collide_pull(const T *__restrict__ fa, const T *__restrict__ ga,
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? LBK_K2_MINB64 : LBK_K2_MINB32) k_collide_pull(const T *__restrict__ fa, const T *__restrict__ ga,
                                                       const T *__restrict__ phi,
                                                       T *__restrict__ fb, T *__restrict__ gb,
                                                       Coll<T> p, int nx, int ny, int nz, long long S)
