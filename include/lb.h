@@ -285,7 +285,7 @@ int lb_batch_run(lb_batch *b, int nsteps);
 int lb_batch_sync(lb_batch *b);
 
 /* Launch shape: threads per CTA (= sites per work item; multiple of 32, at
- * most 512, 256 in FP64) and CTAs per SM (0 = as many as fit; the grid is
+ * most 256) and CTAs per SM (0 = as many as fit; the grid is
  * always co-resident).  Paper: TPB and VVL tuning, Sec. III.C and IV. */
 int lb_batch_set_launch(lb_batch *b, int threads, int ctas_per_sm);
 

@@ -56,11 +56,14 @@ __global__ void __launch_bounds__(256) k_phi_pull(const T *__restrict__ ga, T *_
     phi[s] = phi_site(ga, n, S);
 }
 
+// CTAs per SM the register budget of the collide/stream kernel must allow
+// (measured: FP64 is bound by the FP64 pipe at 2 or 3; an allowance of 1
+// lets ptxas spend 152 registers and loses 11 %; FP32 is DRAM-bound)
 #ifndef LBK_K2_MINB64
-#define LBK_K2_MINB64 1   // FP64 collide/stream: CTAs per SM the register budget must allow
+#define LBK_K2_MINB64 2
 #endif
 #ifndef LBK_K2_MINB32
-#define LBK_K2_MINB32 1
+#define LBK_K2_MINB32 3
 #endif
 
 template <typename T, bool SH>

@@ -106,7 +106,7 @@ def _batch_key(batch) -> str:
 
 
 def batch_candidates(precision):
-    threads = (128, 256) if precision == "fp64" else (128, 256, 512)
+    threads = (128, 256)
     return [(t, c) for t in threads for c in (0, 1, 2, 3)]
 
 
