@@ -80,9 +80,11 @@ enum {
                                copies into a 3-buffer shared-memory pipeline   */
     LB_KERNEL_SLAB = 4,     /* single pass, per z-slab: phi of the slab into
                                shared memory, then a barrier-free collision    */
-    LB_KERNEL_LAG = 5       /* single pass, lagged pipeline: the CTA with
+    LB_KERNEL_LAG = 5,      /* single pass, lagged pipeline: the CTA with
                                ticket c computes phi of site block c and
                                collides block c - D; bounded waits            */
+    LB_KERNEL_TAUG1 = 6     /* tau_g = 1 only: g kept as (phi, mu, u), whose
+                               equilibria it is exactly; ~49 words per site   */
 };
 
 typedef struct lb_ctx lb_ctx;
@@ -175,7 +177,14 @@ int lb_set_state(lb_ctx *c, const double *f, const double *g, int ptr_kind);
  * block_y threads per CTA and z_chunk planes per CTA of the fused, staged
  * and slab kernels (0 = library default for any of the three).  For
  * LB_KERNEL_LAG block_x must be 0 or 256, block_y 0 or 1, and z_chunk is the
- * lag slack in site blocks beyond the stencil's reach (0 = default 128).  Validated against the
+ * lag slack in site blocks beyond the stencil's reach (0 = default 128).
+ * LB_KERNEL_TAUG1 requires tau_g == 1 (LB_ERR_INVALID otherwise) and
+ * converts the stored state to its reduced form (selecting another kernel
+ * converts back).  In that form lb_set_state keeps g only through
+ * phi = sum_i g_i (all the tau_g = 1 dynamics uses) and lb_get_state reports
+ * g as the streamed equilibria of the previous step (after lb_init or
+ * lb_set_state: the equilibrium at each site).  Ensemble members refuse
+ * lb_set_kernel.  Validated against the
  * kernel's limits; LB_ERR_INVALID otherwise.  Paper: the tunable VVL and TPB
  * of TARGET_TLP / TARGET_LAUNCH, Sec. III.C. */
 int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk);

@@ -31,6 +31,7 @@ LB_KERNEL_FUSED = 2
 LB_KERNEL_STAGED = 3
 LB_KERNEL_SLAB = 4
 LB_KERNEL_LAG = 5
+LB_KERNEL_TAUG1 = 6
 
 
 class lb_params(ctypes.Structure):

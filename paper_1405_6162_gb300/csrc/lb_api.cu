@@ -298,12 +298,17 @@ int lb_init(lb_ctx *c, const double *phi0, const double *u0, int ptr_kind)
 {
     if (!c || !phi0 || (ptr_kind != LB_HOST && ptr_kind != LB_DEVICE)) return LB_ERR_INVALID;
     const size_t nb = (size_t)c->N * sizeof(double);
-    if (ptr_kind == LB_DEVICE) return lbk::launch_init(c, phi0, u0);
+    if (ptr_kind == LB_DEVICE) {
+        int rc = lbk::launch_init(c, phi0, u0);
+        if (!rc && c->reduced) rc = lbk::taug1_convert(c, 1);
+        return rc;
+    }
     int rc = ensure_io(c);
     if (rc) return rc;
     rc = copy(c, c->io, phi0, nb, cudaMemcpyHostToDevice);
     if (!rc && u0) rc = copy(c, c->io + c->N, u0, 3 * nb, cudaMemcpyHostToDevice);
     if (!rc) rc = lbk::launch_init(c, c->io, u0 ? c->io + c->N : nullptr);
+    if (!rc && c->reduced) rc = lbk::taug1_convert(c, 1);
     if (!rc) rc = sync(c);
     return rc;
 }
@@ -312,21 +317,25 @@ int lb_step(lb_ctx *c, int nsteps)
 {
     if (!c || nsteps < 0 || c->batch_owned) return LB_ERR_INVALID;
     if (nsteps == 0) return LB_OK;
+    if (c->reduced) return lbk::launch_step_taug1(c, nsteps);
     if (c->kernel == LB_KERNEL_TWO_PASS || c->kernel == LB_KERNEL_AUTO) return lbk::launch_step_two_pass(c, nsteps);
     if (c->kernel == LB_KERNEL_STAGED) return lbk::launch_step_staged(c, nsteps);
     if (c->kernel == LB_KERNEL_SLAB) return lbk::launch_step_slab(c, nsteps);
     if (c->kernel == LB_KERNEL_LAG) return lbk::launch_step_lag(c, nsteps);
+    if (c->reduced) return lbk::launch_step_taug1(c, nsteps);
     return lbk::launch_step_fused(c, nsteps);
 }
 
 int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk)
 {
     if (!c) return LB_ERR_INVALID;
-    if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_LAG) return LB_ERR_INVALID;
+    if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_TAUG1 || c->batch_owned) return LB_ERR_INVALID;
     if (block_x < 0 || block_y < 0 || z_chunk < 0) return LB_ERR_INVALID;
     if (kernel == LB_KERNEL_STAGED) {
         int rc = lbk::staged_validate(c->p.precision, block_x, block_y, z_chunk);
         if (rc) return rc;
+    } else if (kernel == LB_KERNEL_TAUG1) {
+        if (c->p.tau_g != 1.0 || block_x || block_y || z_chunk) return LB_ERR_INVALID;
     } else if (kernel == LB_KERNEL_LAG) {
         int rc = lbk::lag_validate(block_x, block_y, z_chunk);
         if (rc) return rc;
@@ -336,6 +345,12 @@ int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk)
     } else if (kernel == LB_KERNEL_FUSED) {
         int rc = lbk::fused_validate(c->p.precision, block_x, block_y, z_chunk);
         if (rc) return rc;
+    }
+    const int want_reduced = kernel == LB_KERNEL_TAUG1;
+    if (want_reduced != c->reduced) {
+        const int rc = lbk::taug1_convert(c, want_reduced);
+        if (rc) return rc;
+        c->reduced = want_reduced;
     }
     c->kernel = kernel;
     c->block_x = block_x;
@@ -348,11 +363,21 @@ int lb_moments(lb_ctx *c, double *rho, double *u, double *phi, int ptr_kind)
 {
     if (!c || (ptr_kind != LB_HOST && ptr_kind != LB_DEVICE)) return LB_ERR_INVALID;
     if (!rho && !u && !phi) return LB_OK;
-    if (ptr_kind == LB_DEVICE) return lbk::launch_moments(c, rho, u, phi);
+    if (ptr_kind == LB_DEVICE) {
+        if (!c->reduced) return lbk::launch_moments(c, rho, u, phi);
+        int rc = (rho || u) ? lbk::launch_moments(c, rho, u, nullptr) : LB_OK;
+        if (!rc && phi) rc = lbk::taug1_phi_out(c, phi);
+        return rc;
+    }
     int rc = ensure_io(c);
     if (rc) return rc;
     const size_t N = (size_t)c->N, nb = N * sizeof(double);
-    rc = lbk::launch_moments(c, rho ? c->io : nullptr, u ? c->io + N : nullptr, phi ? c->io + 4 * N : nullptr);
+    if (c->reduced) {
+        rc = (rho || u) ? lbk::launch_moments(c, rho ? c->io : nullptr, u ? c->io + N : nullptr, nullptr) : LB_OK;
+        if (!rc && phi) rc = lbk::taug1_phi_out(c, c->io + 4 * N);
+    } else {
+        rc = lbk::launch_moments(c, rho ? c->io : nullptr, u ? c->io + N : nullptr, phi ? c->io + 4 * N : nullptr);
+    }
     if (!rc && rho) rc = copy(c, rho, c->io, nb, cudaMemcpyDeviceToHost);
     if (!rc && u) rc = copy(c, u, c->io + N, 3 * nb, cudaMemcpyDeviceToHost);
     if (!rc && phi) rc = copy(c, phi, c->io + 4 * N, nb, cudaMemcpyDeviceToHost);
@@ -375,7 +400,12 @@ int lb_reduce(lb_ctx *c, double out[5])
 int lb_get_state(lb_ctx *c, double *f, double *g, int ptr_kind)
 {
     if (!c || (ptr_kind != LB_HOST && ptr_kind != LB_DEVICE)) return LB_ERR_INVALID;
-    if (ptr_kind == LB_DEVICE) return lbk::launch_get_state(c, f, g);
+    if (ptr_kind == LB_DEVICE) {
+        if (!c->reduced) return lbk::launch_get_state(c, f, g);
+        int rc = f ? lbk::launch_get_state(c, f, nullptr) : LB_OK;
+        if (!rc && g) rc = lbk::taug1_g_rows(c, 0, lbk::Q, g);
+        return rc;
+    }
     int rc = ensure_io(c);
     if (rc) return rc;
     const size_t N = (size_t)c->N;
@@ -384,7 +414,8 @@ int lb_get_state(lb_ctx *c, double *f, double *g, int ptr_kind)
         if (!dst[which]) continue;
         for (int i0 = 0; i0 < lbk::Q && !rc; i0 += 5) {
             const int i1 = i0 + 5 < lbk::Q ? i0 + 5 : lbk::Q;
-            rc = lbk::launch_rows(c, which, i0, i1, c->io, 0);
+            rc = (which == 1 && c->reduced) ? lbk::taug1_g_rows(c, i0, i1, c->io)
+                                            : lbk::launch_rows(c, which, i0, i1, c->io, 0);
             if (!rc) rc = copy(c, dst[which] + (size_t)i0 * N, c->io, (size_t)(i1 - i0) * N * sizeof(double),
                                cudaMemcpyDeviceToHost);
             if (!rc) rc = sync(c);
@@ -396,7 +427,11 @@ int lb_get_state(lb_ctx *c, double *f, double *g, int ptr_kind)
 int lb_set_state(lb_ctx *c, const double *f, const double *g, int ptr_kind)
 {
     if (!c || (ptr_kind != LB_HOST && ptr_kind != LB_DEVICE)) return LB_ERR_INVALID;
-    if (ptr_kind == LB_DEVICE) return lbk::launch_set_state(c, f, g);
+    if (ptr_kind == LB_DEVICE) {
+        int rc = lbk::launch_set_state(c, f, g);
+        if (!rc && c->reduced && g) rc = lbk::taug1_convert(c, 1);
+        return rc;
+    }
     int rc = ensure_io(c);
     if (rc) return rc;
     const size_t N = (size_t)c->N;
@@ -411,6 +446,8 @@ int lb_set_state(lb_ctx *c, const double *f, const double *g, int ptr_kind)
             if (!rc) rc = sync(c);
         }
     }
+    if (!rc && c->reduced && g) rc = lbk::taug1_convert(c, 1);
+    if (!rc) rc = sync(c);
     return rc;
 }
 

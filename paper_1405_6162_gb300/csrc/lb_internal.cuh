@@ -45,7 +45,9 @@ struct lb_ctx {
     long long wait_timeout_ns = 1000000000LL; // bound of every device-side wait
     double *adj = nullptr;        // [6N] adjoint scratch (lazy): phi_bar, d_bar (3), lap_bar, phi
     double *adj_part = nullptr;   // per-CTA partial dJ/dkappa
-    int batch_owned = 0;                      // member of an lb_batch: stepped and freed by it
+    int batch_owned = 0;
+    int reduced = 0;      // tau_g = 1 form: g kept as (phi, mu, u), see lb_taug1.cu
+    int m_valid = 0;      // reduced form: the previous step's (mu, u) are present                      // member of an lb_batch: stepped and freed by it
     int kernel = LB_KERNEL_AUTO;
     int block_x = 0, block_y = 0, z_chunk = 0;
     lb_alloc_fn alloc = nullptr;
@@ -105,7 +107,7 @@ int launch_get_state(lb_ctx *c, double *f, double *g);
 int launch_set_state(lb_ctx *c, const double *f, const double *g);
 // rows [i0, i1) of f (which = 0) or g (which = 1): dir 0 = out of the state, 1 = into it
 int launch_rows(lb_ctx *c, int which, int i0, int i1, double *buf, int dir);
-int launch_reduce(lb_ctx *c, double *dev_out5);
+int launch_reduce(lb_ctx *c, double *dev_out5);   // reduced form: phi from component 0
 
 // fused kernel (lb_fused.cu)
 int launch_step_fused(lb_ctx *c, int nsteps);
@@ -121,6 +123,12 @@ int launch_adjoint_step(lb_ctx *c, const double *f, const double *g, const doubl
                         double *af_out, double *ag_out, double *dkappa, double *aux, double *kpart);
 int launch_adjoint_init(lb_ctx *c, const double *phi0, const double *u0, const double *af0, const double *ag0,
                         double *phi0_bar, double *dkappa, double *aux, double *kpart);
+
+// tau_g = 1 reduced form (lb_taug1.cu)
+int launch_step_taug1(lb_ctx *c, int nsteps);
+int taug1_convert(lb_ctx *c, int to_reduced);
+int taug1_g_rows(lb_ctx *c, int i0, int i1, double *out);
+int taug1_phi_out(lb_ctx *c, double *out);
 
 // lagged kernel (lb_lag.cu)
 int launch_step_lag(lb_ctx *c, int nsteps);

@@ -179,7 +179,7 @@ __device__ __forceinline__ void block_sum(double (&acc)[K], double *out)
 template <typename T>
 __global__ void __launch_bounds__(kReduceThreads) k_reduce_partial(const T *__restrict__ fa,
                                                                    const T *__restrict__ ga,
-                                                                   long long N, long long S,
+                                                                   long long N, long long S, int g_rows,
                                                                    double *__restrict__ partial)
 {
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_partial(const T *__re
 #pragma unroll
         for (int i = 0; i < Q; i++) {
             f[i] = double(fa[(size_t)i * S + s]);
-            g[i] = double(ga[(size_t)i * S + s]);
+            g[i] = i < g_rows ? double(ga[(size_t)i * S + s]) : 0.0;   // reduced form: phi in row 0
         }
         double R, jx, jy, jz;
         density_moments(f, R, jx, jy, jz);
@@ -345,10 +345,10 @@ int launch_reduce(lb_ctx *c, double *dev_out5)
     const double off = c->p.precision == LB_FP32_SHIFTED ? double(c->N) * c->p.rho0 : 0.0;
     if (c->p.precision == LB_FP64)
         k_reduce_partial<double><<<kReduceBlocks, kReduceThreads, 0, c->stream>>>(
-            (const double *)c->buf.f[cur], (const double *)c->buf.g[cur], c->N, c->S, c->partial);
+            (const double *)c->buf.f[cur], (const double *)c->buf.g[cur], c->N, c->S, c->reduced ? 1 : Q, c->partial);
     else
         k_reduce_partial<float><<<kReduceBlocks, kReduceThreads, 0, c->stream>>>(
-            (const float *)c->buf.f[cur], (const float *)c->buf.g[cur], c->N, c->S, c->partial);
+            (const float *)c->buf.f[cur], (const float *)c->buf.g[cur], c->N, c->S, c->reduced ? 1 : Q, c->partial);
     int rc = check_launch();
     if (rc) return rc;
     k_reduce_final<<<1, kReduceThreads, 0, c->stream>>>(c->partial, kReduceBlocks, off, dev_out5);
