@@ -450,7 +450,7 @@ def main():
                     help="run only timesteps of one lattice (profiling case)")
     ap.add_argument("--lattice", type=int, default=128, help="edge of the --only lattice")
     ap.add_argument("--precision", choices=["fp32_shifted", "fp64"], default="fp32_shifted")
-    ap.add_argument("--kernel", choices=["two_pass", "fused", "staged", "slab", "lag"], default=None,
+    ap.add_argument("--kernel", choices=["two_pass", "fused", "staged", "slab", "lag", "taug1"], default=None,
                     help="override the tuned launch of the --only lattice")
     ap.add_argument("--block", type=int, nargs=3, default=(0, 0, 0), metavar=("BX", "BY", "ZC"))
     args = ap.parse_args()
