@@ -74,22 +74,74 @@ k_t1_collide(const T *__restrict__ fa, T *__restrict__ ga /* level a: phi in, mu
     ga[4 * S + s] = jz * rinv;
 }
 
+// Moments of one site, and the equilibria of the (up to three) directions
+// that share a source row, i.e. the same (c_y, c_z): c_x = 0, +1, -1.
+template <typename T>
+struct SrcM {
+    T ph, gmh, ux, uy, uz;   // phi, 9/2 (Gamma mu - phi/3), u
+};
+
+template <typename T>
+__device__ __forceinline__ SrcM<T> load_m(const T *__restrict__ ga, long long S, long long src, T gamma)
+{
+    SrcM<T> m;
+    m.ph = ga[src];
+    m.gmh = T(4.5) * (gamma * ga[S + src] - m.ph * T(1.0 / 3.0));
+    m.ux = ga[2 * S + src];
+    m.uy = ga[3 * S + src];
+    m.uz = ga[4 * S + src];
+    return m;
+}
+
+// geq for direction (cx, cy, cz) at a source with moments m:
+//   w [phi (1 - 3/2 u^2) + 3 phi c.u + 9/2 phi (c.u)^2 + gmh (c^2 - 1)]
+template <typename T>
+__device__ __forceinline__ T geq_m(const SrcM<T> &m, int cxv, int cyv, int czv, T w)
+{
+    const T cu = T(cxv) * m.ux + T(cyv) * m.uy + T(czv) * m.uz;
+    const T base = m.ph * (T(1) - T(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz));
+    const T c2m1 = T(cxv * cxv + cyv * cyv + czv * czv - 1);
+    return w * (base + m.gmh * c2m1 + cu * (T(3) * m.ph + T(4.5) * m.ph * cu));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kT1Threads) k_t1_phi(const T *__restrict__ ga, T *__restrict__ gb, Coll<T> p,
                                                         int nx, int ny, int nz, long long S)
 {
     const long long N = (long long)nx * ny * nz;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= N) return;
+    const int s0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = s0 < N;
+    const int s = live ? s0 : (int)(N - 1);           // dead lanes mirror the last site
     const Nbr n(s, nx, ny, nz);
-    T g[Q];
+    const int lane = threadIdx.x & 31;
+    const int x = n.X[1];
+    // the lane below / above holds x - 1 / x + 1 of the same row
+    const bool from_below = lane > 0 && x > 0 && live;
+    const bool from_above = lane < 31 && x + 1 < nx && s0 + 1 < N;
+    T acc = T(0);
+    // (c_y, c_z) of the 9 source rows; dirs with that (c_y, c_z) and c_x = 0, +1, -1
 #pragma unroll
-    for (int i = 0; i < Q; i++) {
-        const int src = n.src(i);
-        const T ph = ga[src], mu = ga[S + src];
-        g[i] = geq_dir<T>(i, ph, p.gamma * mu - ph * T(1.0 / 3.0), ga[2 * S + src], ga[3 * S + src], ga[4 * S + src]);
+    for (int r = 0; r < 9; r++) {
+        const int cyv = r == 0 ? 0 : (r == 1 ? 1 : (r == 2 ? -1 : (r == 3 || r == 4 ? 0 : (r == 5 || r == 7 ? 1 : -1))));
+        const int czv = r < 3 ? 0 : (r == 3 ? 1 : (r == 4 ? -1 : (r == 5 || r == 8 ? 1 : -1)));
+        const bool three = r < 5;                    // rows with c_x = 0, +1, -1 (else c_x = 0 only)
+        const T w0 = T(r == 0 ? 1.0 / 3.0 : (r < 5 ? 1.0 / 18.0 : 1.0 / 36.0));
+        const T w1 = T(r == 0 ? 1.0 / 18.0 : 1.0 / 36.0);
+        // pull: the source of direction c is x - c; own column of this row
+        const long long row = (long long)n.Y[1 - cyv] + n.Z[1 - czv];
+        const SrcM<T> m = load_m(ga, S, row + x, p.gamma);
+        acc += geq_m(m, 0, cyv, czv, w0);
+        if (three) {
+            // direction (+1, cy, cz) takes its value from x - 1: computed by the lane below
+            const T vp = geq_m(m, 1, cyv, czv, w1);
+            const T vm = geq_m(m, -1, cyv, czv, w1);
+            const T up = __shfl_up_sync(0xffffffffu, vp, 1);
+            const T dn = __shfl_down_sync(0xffffffffu, vm, 1);
+            acc += from_below ? up : geq_m(load_m(ga, S, row + n.X[0], p.gamma), 1, cyv, czv, w1);
+            acc += from_above ? dn : geq_m(load_m(ga, S, row + n.X[2], p.gamma), -1, cyv, czv, w1);
+        }
     }
-    gb[s] = sum19(g);
+    if (live) gb[s] = acc;
 }
 
 // g state of the reduced form as post-streaming FP64 rows [i0, i1):
