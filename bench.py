@@ -34,6 +34,9 @@ import lb_inputs as LI  # noqa: E402
 
 DIMS = (256, 256, 256)
 BYTES_PER_SITE = {"fp32_shifted": 4 * 19 * 4, "fp64": 4 * 19 * 8}   # read+write f and g once
+# tau_g = 1 reduced form: collide reads f (19) + phi, writes f (19) + (gmh, u) (4);
+# the phi pass reads phi + (gmh, u) and writes phi -- 49 words per site
+BYTES_PER_SITE_TAUG1 = {"fp32_shifted": 49 * 4, "fp64": 49 * 8}
 METRIC = "MLUPS and % of HBM roofline (fused step), FP32-shifted vs FP64 at stated error"
 ORACLE_SAMPLE = (64, 64, 64)
 ORACLE_STEPS = 30
@@ -42,7 +45,8 @@ FALLBACK_HBM = 6800.0
 # kernels one timestep launches, per lb_set_kernel choice
 STEP_KERNELS = {"auto": "timestep = k_phi_pull + k_collide_pull (two launches)",
                 "two_pass": "timestep = k_phi_pull + k_collide_pull (two launches)",
-                "fused": "k_fused", "staged": "k_staged", "slab": "k_slab", "lag": "k_lag"}
+                "fused": "k_fused", "staged": "k_staged", "slab": "k_slab", "lag": "k_lag",
+                "taug1": "timestep = k_t1_collide + k_t1_phi (two launches)"}
 
 
 def _dist():
@@ -66,10 +70,10 @@ def _peaks():
 STEP_SOURCES = ("d3q19.cuh", "lb_site.cuh", "lb_internal.cuh", "lb_kernels.cu")
 
 
-def _kernel_sha():
+def _kernel_sha(sources=STEP_SOURCES):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1405_6162_gb300", "csrc")
-    for name in STEP_SOURCES:
+    for name in sources:
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(name.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -78,15 +82,18 @@ def _kernel_sha():
 def _profile_value(name, key, need_current=True):
     """A number recorded in a committed ncu summary (profiles/<name>.md, a
     line "key: value"); None if absent or, when ``need_current``, if the
-    summary was taken on other kernel sources than the current ones."""
+    summary was taken on other kernel sources than the current ones (the
+    summary's "(sources: ...)" line, else the default timestep's)."""
     path = os.path.join(ROOT, "profiles", f"{name}.md")
     try:
         txt = open(path).read()
     except OSError:
         return None
     m_sha = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", txt)
+    m_src = re.search(r"\(sources:\s*([^)]*)\)", txt)
+    sources = tuple(x.strip() for x in m_src.group(1).split(",")) if m_src else STEP_SOURCES
     m_v = re.search(rf"^{re.escape(key)}:\s*([0-9.eE+-]+)", txt, re.M)
-    if not m_v or (need_current and (not m_sha or m_sha.group(1) != _kernel_sha())):
+    if not m_v or (need_current and (not m_sha or m_sha.group(1) != _kernel_sha(sources))):
         return None
     return float(m_v.group(1))
 
@@ -298,6 +305,26 @@ def run_ours(args):
         results[prec] = dict(cfg=cfg, wall=wall, t_launch=t_launch, clocks=clk.summary(),
                              mass=float(r[0]))
 
+    # the tau_g = 1 reduced form on the same workload (the workload has tau_g = 1)
+    reduced = {}
+    for prec in ("fp32_shifted", "fp64"):
+        with Lattice.from_params(DIMS, params, precision=prec) as lat:
+            lat.set_kernel("taug1")
+            lat.init(phi0)
+            lat.step(args.warmup)
+            barrier()
+            start = torch.cuda.Event(enable_timing=True)
+            stop = torch.cuda.Event(enable_timing=True)
+            k = args.steps if prec == "fp32_shifted" else max(1, args.steps // 4)
+            with Clocks(local) as clk:
+                start.record()
+                lat.step(k)
+                stop.record()
+                barrier()
+            wall = max_over_ranks(start.elapsed_time(stop) / 1e3)
+            per = _time_steps(lat, max(5, min(k, 20)), torch)
+        reduced[prec] = dict(wall=wall, steps=k, t_launch=float(np.mean(per)), clocks=clk.summary())
+
     # end to end through the C ABI with host buffers (pinned), copies timed
     prec = "fp32_shifted"
     phi_host = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
@@ -354,6 +381,19 @@ def run_ours(args):
                     "hbm_frac": BYTES_PER_SITE[prec] * n / r["t_launch"] / 1e9 / peak}
         return mlups, roof
 
+    def reduced_for(prec):
+        r = reduced[prec]
+        bpl = BYTES_PER_SITE_TAUG1[prec] * n
+        achieved = bpl / r["t_launch"] / 1e9
+        return {"value": ws * n * r["steps"] / r["wall"] / 1e6, "unit": "MLUPS", "steps": r["steps"],
+                "ms_per_step": r["wall"] / r["steps"] * 1e3, "clocks": r["clocks"],
+                "roofline": {"bound": "hbm" if prec == "fp32_shifted" else "alu (FP64 pipe)",
+                             "kernel": STEP_KERNELS["taug1"], "achieved": achieved, "peak": peak,
+                             "unit": "GB/s", "frac": achieved / peak,
+                             "traffic": _profile_value("step_taug1_256cubed", f"dram_bytes_per_step_{prec}"),
+                             "peak_kind": f"{peak_kind} (copy bandwidth)",
+                             "algorithmic_bytes_per_launch": bpl}}
+
     v32, roof32 = line_for("fp32_shifted")
     v64, roof64 = line_for("fp64")
     r32 = results["fp32_shifted"]
@@ -376,6 +416,9 @@ def run_ours(args):
         "error_vs_oracle": ({"sample": f"{ORACLE_SAMPLE[0]}^3 spinodal seed 1, {ORACLE_STEPS} steps, "
                                        "max|gpu-oracle| / max|oracle| per field (u: / max sum_i|f_i c_i|/rho)", **errs} if errs else None),
         "clocks": r32["clocks"],
+        "taug1": {"what": "tau_g = 1 reduced form (LB_KERNEL_TAUG1): g kept as phi and (gmh, u), "
+                          "same results as the general step to rounding; valid only at tau_g = 1",
+                  "fp32_shifted": reduced_for("fp32_shifted"), "fp64": reduced_for("fp64")},
         "ensemble": ens,
         "adjoint": adj,
         "e2e": e2e,

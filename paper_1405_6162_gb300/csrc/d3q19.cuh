@@ -148,21 +148,24 @@ __device__ __forceinline__ T sum19(const T (&g)[Q])
          + ((g[16] + g[17]) + g[18]);
 }
 
-// In-place BGK collision of one site given phi and its stencil values:
+// In-place BGK collision of f at one site given phi and its stencil values
+// (also returns u and mu):
 // f*_i = (1 - omega) f_i + omega feq_i with omega feq_i expanded per weight
 // class (rest, face, edge) and per opposite pair, sharing every partial sum.
 template <typename T, bool SH>
-__device__ __forceinline__ void collide(const Coll<T>& p, T (&f)[Q], T (&g)[Q],
-                                        T phi, T dx, T dy, T dz, T lap)
+__device__ __forceinline__ void collide_f(const Coll<T>& p, T (&f)[Q], T phi, T dx, T dy, T dz, T lap,
+                                          T& ux, T& uy, T& uz, T& mu)
 {
     T R, jx, jy, jz;
     density_moments(f, R, jx, jy, jz);
     const T third = T(1.0 / 3.0), h = T(4.5);
     const T rho = SH ? p.rho0 + R : R;
     const T rinv = T(1) / rho;
-    const T ux = jx * rinv, uy = jy * rinv, uz = jz * rinv;
+    ux = jx * rinv;
+    uy = jy * rinv;
+    uz = jz * rinv;
     const T phi2 = phi * phi;
-    const T mu = phi * (p.A + p.B * phi2) - p.kappa * lap;
+    mu = phi * (p.A + p.B * phi2) - p.kappa * lap;
     const T pb = phi2 * (T(0.5) * p.A + T(0.75) * p.B * phi2)
                - p.kappa * (phi * lap + T(0.5) * (dx * dx + dy * dy + dz * dz));
     // S = P + rho u u
@@ -204,6 +207,16 @@ __device__ __forceinline__ void collide(const Coll<T>& p, T (&f)[Q], T (&g)[Q],
     LBK_EDGES(11, 12, 13, 14, Sxx, Szz, Sxz, jx, jz)
     LBK_EDGES(15, 16, 17, 18, Syy, Szz, Syz, jy, jz)
 #undef LBK_EDGES
+}
+
+// In-place BGK collision of f (collide_f) and of g at one site.
+template <typename T, bool SH>
+__device__ __forceinline__ void collide(const Coll<T>& p, T (&f)[Q], T (&g)[Q],
+                                        T phi, T dx, T dy, T dz, T lap)
+{
+    const T third = T(1.0 / 3.0), h = T(4.5);
+    T ux, uy, uz, mu;
+    collide_f<T, SH>(p, f, phi, dx, dy, dz, lap, ux, uy, uz, mu);
 
     // ---- g: omega_g geq_i = omega_g w_i [phi + 3 phi c.u + 9/2 (phi (c.u)^2 - phi u^2/3 + (Gamma mu - phi/3)(c^2 - 1))]
     const T cg = p.cg;

@@ -35,7 +35,7 @@ def _check(got, want, tol, f_oracle):
         assert e <= t, (name, e)
 
 
-@pytest.mark.parametrize("dims", [(32, 32, 32), (13, 7, 5), (1, 1, 9), (40, 9, 35), (2, 3, 2)])
+@pytest.mark.parametrize("dims", [(32, 32, 32), (13, 7, 5), (1, 1, 9), (40, 9, 35), (2, 3, 2), (70, 37, 11)])
 def test_reduced_form_matches_oracle_fp64(dims):
     p = dict(P0, tau=0.8)                          # tau_g = 1
     phi0 = L.spinodal_phi0(*dims, seed=300, amp=0.4)
