@@ -89,15 +89,25 @@ def velocity_set():
     return c.reshape(19, 3), w
 
 
-def gradients(dims, phi, kind="serial"):
-    """(grad [3][N], lap [N]) of phi by the 7-point stencils."""
+STENCILS = (7, 19, 27)
+
+
+def _npts(npts):
+    if npts not in STENCILS:
+        raise ValueError(f"stencil must be one of {STENCILS}")
+    return int(npts)
+
+
+def gradients(dims, phi, kind="serial", npts=7):
+    """(grad [3][N], lap [N]) of phi by the 7-point stencils, or the
+    isotropic 19- / 27-point ones (``npts``)."""
     nx, ny, nz = dims
     n = nx * ny * nz
     phi, pp = _arr(phi, kind)
     grad = np.zeros(3 * n, dtype=_dtype(kind))
     lap = np.zeros(n, dtype=_dtype(kind))
-    _lib(kind).orc_gradients(nx, ny, nz, pp, grad.ctypes.data_as(ctypes.c_void_p),
-                             lap.ctypes.data_as(ctypes.c_void_p))
+    _lib(kind).orc_gradients_n(nx, ny, nz, _npts(npts), pp, grad.ctypes.data_as(ctypes.c_void_p),
+                               lap.ctypes.data_as(ctypes.c_void_p))
     return grad.reshape(3, n), lap
 
 
@@ -128,8 +138,9 @@ def site_equilibrium(params, rho, j, phi, d, lap):
     return feq, geq
 
 
-def init(dims, params, phi0, u0=None, kind="serial"):
-    """Equilibrium initial state (f, g), each [19][N]."""
+def init(dims, params, phi0, u0=None, kind="serial", npts=7):
+    """Equilibrium initial state (f, g), each [19][N] (stencils of ``npts``
+    points for the initial gradients)."""
     nx, ny, nz = dims
     n = nx * ny * nz
     prm, pp = _prm(params, kind)
@@ -140,20 +151,21 @@ def init(dims, params, phi0, u0=None, kind="serial"):
         up = None
     f = np.zeros(19 * n, dtype=_dtype(kind))
     g = np.zeros(19 * n, dtype=_dtype(kind))
-    _lib(kind).orc_init(nx, ny, nz, pp, php, up, f.ctypes.data_as(ctypes.c_void_p),
-                        g.ctypes.data_as(ctypes.c_void_p))
+    _lib(kind).orc_init_n(nx, ny, nz, _npts(npts), pp, php, up, f.ctypes.data_as(ctypes.c_void_p),
+                          g.ctypes.data_as(ctypes.c_void_p))
     return f.reshape(19, n), g.reshape(19, n)
 
 
-def step(dims, params, f, g, nsteps, kind="serial"):
-    """Advance (f, g) by ``nsteps``; returns new arrays (inputs untouched)."""
+def step(dims, params, f, g, nsteps, kind="serial", npts=7):
+    """Advance (f, g) by ``nsteps`` with the ``npts``-point stencils; returns
+    new arrays (inputs untouched)."""
     nx, ny, nz = dims
     n = nx * ny * nz
     prm, pp = _prm(params, kind)
     f = np.array(f, dtype=_dtype(kind), copy=True).reshape(-1)
     g = np.array(g, dtype=_dtype(kind), copy=True).reshape(-1)
-    _lib(kind).orc_step(nx, ny, nz, pp, f.ctypes.data_as(ctypes.c_void_p),
-                        g.ctypes.data_as(ctypes.c_void_p), int(nsteps))
+    _lib(kind).orc_step_n(nx, ny, nz, _npts(npts), pp, f.ctypes.data_as(ctypes.c_void_p),
+                          g.ctypes.data_as(ctypes.c_void_p), int(nsteps))
     return f.reshape(19, n), g.reshape(19, n)
 
 

@@ -29,6 +29,15 @@
  * phi = sum_i g_i, and the 7-point stencils d_a phi = (phi(x+e_a) -
  * phi(x-e_a))/2, lap phi = sum of the 6 face neighbours - 6 phi(x).
  *
+ * The *_n entry points also take the isotropic 19- and 27-point stencils
+ * (the paper only says "standard finite-difference"; these are read as the
+ * lattice-weighted differences over the D3Q19 / D3Q27 neighbourhoods):
+ *   d_a phi = (1/cs2) sum_c W_c c_a phi(x + c),
+ *   lap phi = (2/cs2) sum_c W_c (phi(x + c) - phi(x)),
+ * with the D3Q19 weights above, or the D3Q27 weights 8/27 (rest), 2/27
+ * (faces), 1/54 (edges), 1/216 (corners).  Both reproduce the 7-point
+ * stencils on fields that vary along one axis only.
+ *
  * Distributions are stored SoA: value i of site s at f[i*N + s], with site
  * s = x + nx*(y + ny*z).  The velocity set is built by enumerating (cx,cy,cz)
  * in {-1,0,1}^3 in lexicographic order and keeping |c|^2 <= 2; callers map it
@@ -113,6 +122,43 @@ void orc_gradients(int nx, int ny, int nz, const real *phi, real *grad, real *la
             }
 }
 
+/* Isotropic 19- or 27-point differences (see the header); npts = 7 is
+ * orc_gradients. */
+void orc_gradients_n(int nx, int ny, int nz, int npts, const real *phi, real *grad, real *lap)
+{
+    if (npts == 7) {
+        orc_gradients(nx, ny, nz, phi, grad, lap);
+        return;
+    }
+    long N = (long)nx * ny * nz;
+    const double cs2 = 1.0 / 3.0;
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                long s = site(x, y, z, nx, ny, nz);
+                real d[3] = {0.0, 0.0, 0.0}, l = 0.0;
+                for (int a = -1; a <= 1; a++)
+                    for (int b = -1; b <= 1; b++)
+                        for (int c = -1; c <= 1; c++) {
+                            int c2 = a * a + b * b + c * c;
+                            double W;
+                            if (npts == 19) {
+                                if (c2 > 2) continue;
+                                W = (c2 == 0) ? 1.0 / 3.0 : (c2 == 1) ? 1.0 / 18.0 : 1.0 / 36.0;
+                            } else {
+                                W = (c2 == 0) ? 8.0 / 27.0 : (c2 == 1) ? 2.0 / 27.0 : (c2 == 2) ? 1.0 / 54.0 : 1.0 / 216.0;
+                            }
+                            real v = phi[site(x + a, y + b, z + c, nx, ny, nz)];
+                            d[0] += W * a * v;
+                            d[1] += W * b * v;
+                            d[2] += W * c * v;
+                            l += W * (v - phi[s]);
+                        }
+                for (int a = 0; a < 3; a++) grad[a * N + s] = d[a] / cs2;
+                lap[s] = 2.0 * l / cs2;
+            }
+}
+
 /* Chemical potential and thermodynamic pressure tensor at one site. */
 void orc_site_thermo(const real *prm, real phi, const real *d, real lap,
                      real *mu, real *P /* [3][3] */)
@@ -158,14 +204,14 @@ void orc_site_equilibrium(const real *prm, real rho, const real *j, real phi,
 
 /* f = feq(rho0, rho0 u0, phi0), g = geq(...): the initial state.  u0 is SoA
  * [3][N] or NULL for a fluid at rest. */
-void orc_init(int nx, int ny, int nz, const real *prm, const real *phi0,
-              const real *u0, real *f, real *g)
+void orc_init_n(int nx, int ny, int nz, int npts, const real *prm, const real *phi0,
+                const real *u0, real *f, real *g)
 {
     velocity_set();
     long N = (long)nx * ny * nz;
     real *grad = malloc(sizeof(real) * 3 * N);
     real *lap = malloc(sizeof(real) * N);
-    orc_gradients(nx, ny, nz, phi0, grad, lap);
+    orc_gradients_n(nx, ny, nz, npts, phi0, grad, lap);
     real rho = prm[P_RHO0];
     for (long s = 0; s < N; s++) {
         real j[3], d[3], feq[NV], geq[NV];
@@ -183,8 +229,15 @@ void orc_init(int nx, int ny, int nz, const real *prm, const real *phi0,
     free(lap);
 }
 
-/* nsteps timesteps in place: phi = sum g; stencils; collide f and g; stream. */
-void orc_step(int nx, int ny, int nz, const real *prm, real *f, real *g, int nsteps)
+void orc_init(int nx, int ny, int nz, const real *prm, const real *phi0,
+              const real *u0, real *f, real *g)
+{
+    orc_init_n(nx, ny, nz, 7, prm, phi0, u0, f, g);
+}
+
+/* nsteps timesteps in place: phi = sum g; stencils (npts = 7, 19 or 27
+ * points); collide f and g; stream. */
+void orc_step_n(int nx, int ny, int nz, int npts, const real *prm, real *f, real *g, int nsteps)
 {
     velocity_set();
     long N = (long)nx * ny * nz;
@@ -199,7 +252,7 @@ void orc_step(int nx, int ny, int nz, const real *prm, real *f, real *g, int nst
             for (int i = 0; i < NV; i++) acc += g[i * N + s];
             phi[s] = acc;
         }
-        orc_gradients(nx, ny, nz, phi, grad, lap);
+        orc_gradients_n(nx, ny, nz, npts, phi, grad, lap);
 #pragma omp parallel for
         for (long s = 0; s < N; s++) {
             real rho = 0.0, j[3] = {0.0, 0.0, 0.0}, d[3], feq[NV], geq[NV];
@@ -227,6 +280,11 @@ void orc_step(int nx, int ny, int nz, const real *prm, real *f, real *g, int nst
                 }
     }
     free(phi); free(grad); free(lap); free(fs); free(gs);
+}
+
+void orc_step(int nx, int ny, int nz, const real *prm, real *f, real *g, int nsteps)
+{
+    orc_step_n(nx, ny, nz, 7, prm, f, g, nsteps);
 }
 
 /* rho = sum f, u = sum f c / rho (SoA [3][N]), phi = sum g. */
