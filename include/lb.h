@@ -127,7 +127,8 @@ int lb_create(const lb_params *p, void *cuda_stream, lb_ctx **out);
 void lb_destroy(lb_ctx *c);
 
 /* Initial state: rho = rho0, u = u0 (u0 == NULL: fluid at rest), phi = phi0;
- * the 7-point stencils of phi0 give mu and the pressure tensor, and f, g are
+ * the stencils of phi0 (lb_set_stencil; 7 points by default) give mu and the
+ * pressure tensor, and f, g are
  * set to their equilibria (computed in FP64, then stored in the context's
  * precision).  phi0 is double[N], u0 SoA double[3][N], both in ptr_kind
  * memory; they are read before the call returns (LB_HOST) or before later
@@ -188,6 +189,21 @@ int lb_set_state(lb_ctx *c, const double *f, const double *g, int ptr_kind);
  * kernel's limits; LB_ERR_INVALID otherwise.  Paper: the tunable VVL and TPB
  * of TARGET_TLP / TARGET_LAUNCH, Sec. III.C. */
 int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk);
+
+/* Points of the finite-difference stencils of phi (gradient and Laplacian)
+ * used by later lb_init and lb_step calls: 7 (default) = nearest faces,
+ * d_a phi = (phi(x + e_a) - phi(x - e_a))/2, lap phi = sum of the 6 face
+ * neighbours - 6 phi(x); 19 or 27 = the isotropic lattice-weighted
+ * differences d_a phi = 3 sum_c W_c c_a phi(x + c),
+ * lap phi = 6 sum_c W_c (phi(x + c) - phi(x)) over the D3Q19 (W = 1/18
+ * faces, 1/36 edges) or D3Q27 (2/27, 1/54, 1/216 corners) neighbourhood.
+ * The stored state is unchanged.  19 and 27 run on LB_KERNEL_AUTO,
+ * LB_KERNEL_TWO_PASS and LB_KERNEL_TAUG1; LB_ERR_INVALID for another
+ * points value, for the other kernels (now or in a later lb_set_kernel), for
+ * ensemble members, and lb_adjoint_* refuse contexts set to 19 or 27.
+ * Paper: the "standard finite-difference" order-parameter update, Sec. II.A
+ * (which names no stencil). */
+int lb_set_stencil(lb_ctx *c, int points);
 
 /* Synchronise the context's stream; returns LB_ERR_TIMEOUT if a bounded
  * device-side wait (the lagged kernel's inter-CTA waits) gave up since the

@@ -60,6 +60,7 @@ SIGNATURES = {
     "lb_get_state": (_I, [_P, _P, _P, _I]),
     "lb_set_state": (_I, [_P, _P, _P, _I]),
     "lb_set_kernel": (_I, [_P, _I, _I, _I, _I]),
+    "lb_set_stencil": (_I, [_P, _I]),
     "lb_get_info": (_I, [_P, _P, _P, _P, _P]),
     "lb_sync": (_I, [_P]),
     "lb_set_wait_timeout": (_I, [_P, ctypes.c_longlong]),

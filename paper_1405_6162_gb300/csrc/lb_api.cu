@@ -247,7 +247,8 @@ static int ensure_adj(lb_ctx *c)
 int lb_adjoint_step(lb_ctx *c, const double *f, const double *g, const double *af_in, const double *ag_in,
                     double *af_out, double *ag_out, double *dkappa)
 {
-    if (!c || c->p.precision != LB_FP64 || !f || !g || !af_in || !ag_in || !af_out || !ag_out || !dkappa)
+    if (!c || c->p.precision != LB_FP64 || c->npts != 7 || !f || !g || !af_in || !ag_in || !af_out || !ag_out ||
+        !dkappa)
         return LB_ERR_INVALID;
     if (af_out == af_in || ag_out == ag_in || af_out == ag_in || ag_out == af_in) return LB_ERR_INVALID;
     const int rc = ensure_adj(c);
@@ -258,7 +259,8 @@ int lb_adjoint_step(lb_ctx *c, const double *f, const double *g, const double *a
 int lb_adjoint_init(lb_ctx *c, const double *phi0, const double *u0, const double *af0, const double *ag0,
                     double *phi0_bar, double *dkappa)
 {
-    if (!c || c->p.precision != LB_FP64 || !phi0 || !af0 || !ag0 || !phi0_bar || !dkappa) return LB_ERR_INVALID;
+    if (!c || c->p.precision != LB_FP64 || c->npts != 7 || !phi0 || !af0 || !ag0 || !phi0_bar || !dkappa)
+        return LB_ERR_INVALID;
     const int rc = ensure_adj(c);
     if (rc) return rc;
     return lbk::launch_adjoint_init(c, phi0, u0, af0, ag0, phi0_bar, dkappa, c->adj, c->adj_part);
@@ -322,8 +324,23 @@ int lb_step(lb_ctx *c, int nsteps)
     if (c->kernel == LB_KERNEL_STAGED) return lbk::launch_step_staged(c, nsteps);
     if (c->kernel == LB_KERNEL_SLAB) return lbk::launch_step_slab(c, nsteps);
     if (c->kernel == LB_KERNEL_LAG) return lbk::launch_step_lag(c, nsteps);
-    if (c->reduced) return lbk::launch_step_taug1(c, nsteps);
     return lbk::launch_step_fused(c, nsteps);
+}
+
+// kernels whose phi stencil is fixed to 7 points (staged in shared memory)
+static bool seven_point_only(int kernel)
+{
+    return kernel == LB_KERNEL_FUSED || kernel == LB_KERNEL_STAGED || kernel == LB_KERNEL_SLAB ||
+           kernel == LB_KERNEL_LAG;
+}
+
+int lb_set_stencil(lb_ctx *c, int points)
+{
+    if (!c || c->batch_owned) return LB_ERR_INVALID;
+    if (points != 7 && points != 19 && points != 27) return LB_ERR_INVALID;
+    if (points != 7 && seven_point_only(c->kernel)) return LB_ERR_INVALID;
+    c->npts = points;
+    return LB_OK;
 }
 
 int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk)
@@ -331,6 +348,7 @@ int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk)
     if (!c) return LB_ERR_INVALID;
     if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_TAUG1 || c->batch_owned) return LB_ERR_INVALID;
     if (block_x < 0 || block_y < 0 || z_chunk < 0) return LB_ERR_INVALID;
+    if (c->npts != 7 && seven_point_only(kernel)) return LB_ERR_INVALID;
     if (kernel == LB_KERNEL_STAGED) {
         int rc = lbk::staged_validate(c->p.precision, block_x, block_y, z_chunk);
         if (rc) return rc;

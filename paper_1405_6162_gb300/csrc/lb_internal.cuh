@@ -45,9 +45,10 @@ struct lb_ctx {
     long long wait_timeout_ns = 1000000000LL; // bound of every device-side wait
     double *adj = nullptr;        // [6N] adjoint scratch (lazy): phi_bar, d_bar (3), lap_bar, phi
     double *adj_part = nullptr;   // per-CTA partial dJ/dkappa
-    int batch_owned = 0;
-    int reduced = 0;      // tau_g = 1 form: g kept as (phi, mu, u), see lb_taug1.cu
-    int m_valid = 0;      // reduced form: the previous step's (mu, u) are present                      // member of an lb_batch: stepped and freed by it
+    int batch_owned = 0;  // member of an lb_batch: stepped and freed by it
+    int reduced = 0;      // tau_g = 1 form: g kept as phi and (gmh, u), see lb_taug1.cu
+    int m_valid = 0;      // reduced form: the previous step's (gmh, u) are present
+    int npts = 7;         // points of the phi stencil: 7, 19 or 27 (lb_set_stencil)
     int kernel = LB_KERNEL_AUTO;
     int block_x = 0, block_y = 0, z_chunk = 0;
     lb_alloc_fn alloc = nullptr;

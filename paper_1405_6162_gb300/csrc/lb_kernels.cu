@@ -17,7 +17,7 @@ namespace lbk {
 
 // ------------------------------------------------------------------ init
 
-template <typename T, bool SH>
+template <typename T, bool SH, int NP>
 __global__ void __launch_bounds__(256) k_init(const double *__restrict__ phi0,
                                               const double *__restrict__ u0,
                                               T *__restrict__ fa, T *__restrict__ ga,
@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(256) k_init(const double *__restrict__ phi0,
     const Nbr n(s, nx, ny, nz);
     const double ph = phi0[s];
     double dx, dy, dz, lap;
-    stencil(phi0, n, ph, dx, dy, dz, lap);
+    stencil_np<NP, double>(phi0, n, ph, dx, dy, dz, lap);
     const double jx = u0 ? p.rho0 * u0[s] : 0.0;
     const double jy = u0 ? p.rho0 * u0[N + s] : 0.0;
     const double jz = u0 ? p.rho0 * u0[2 * N + s] : 0.0;
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) k_phi_pull(const T *__restrict__ ga, T *_
 #define LBK_K2_MINB32 3
 #endif
 
-template <typename T, bool SH>
+template <typename T, bool SH, int NP = 7>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? LBK_K2_MINB64 : LBK_K2_MINB32) k_collide_pull(const T *__restrict__ fa, const T *__restrict__ ga,
                                                       const T *__restrict__ phi,
                                                       T *__restrict__ fb, T *__restrict__ gb,
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? LBK_K2_MINB64 : LBK_K2_M
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
     const Nbr n(s, nx, ny, nz);
-    collide_site<T, SH>(fa, ga, phi, fb, gb, p, n, s, S);
+    collide_site<T, SH, NP>(fa, ga, phi, fb, gb, p, n, s, S);
 }
 
 // ------------------------------------------------------------------ moments / state
@@ -223,21 +223,36 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_final(const double *_
 
 static inline unsigned grid_for(long long N, int tpb) { return (unsigned)((N + tpb - 1) / tpb); }
 
-int launch_init(lb_ctx *c, const double *phi0_d, const double *u0_d)
+template <typename T, bool SH, int NP>
+static void init_np(lb_ctx *c, const double *phi0_d, const double *u0_d)
 {
-    const auto p = make_coll<double>(c->p);
     const int cur = c->buf.cur;
-    const unsigned grid = grid_for(c->N, 256);
-    if (c->p.precision == LB_FP64)
-        k_init<double, false><<<grid, 256, 0, c->stream>>>(phi0_d, u0_d, (double *)c->buf.f[cur],
-                                                           (double *)c->buf.g[cur], p, c->p.nx, c->p.ny, c->p.nz, c->S);
-    else
-        k_init<float, true><<<grid, 256, 0, c->stream>>>(phi0_d, u0_d, (float *)c->buf.f[cur],
-                                                         (float *)c->buf.g[cur], p, c->p.nx, c->p.ny, c->p.nz, c->S);
-    return check_launch();
+    k_init<T, SH, NP><<<grid_for(c->N, 256), 256, 0, c->stream>>>(phi0_d, u0_d, (T *)c->buf.f[cur],
+                                                                  (T *)c->buf.g[cur], make_coll<double>(c->p),
+                                                                  c->p.nx, c->p.ny, c->p.nz, c->S);
 }
 
 template <typename T, bool SH>
+static void init_t(lb_ctx *c, const double *phi0_d, const double *u0_d)
+{
+    if (c->npts == 19)
+        init_np<T, SH, 19>(c, phi0_d, u0_d);
+    else if (c->npts == 27)
+        init_np<T, SH, 27>(c, phi0_d, u0_d);
+    else
+        init_np<T, SH, 7>(c, phi0_d, u0_d);
+}
+
+int launch_init(lb_ctx *c, const double *phi0_d, const double *u0_d)
+{
+    if (c->p.precision == LB_FP64)
+        init_t<double, false>(c, phi0_d, u0_d);
+    else
+        init_t<float, true>(c, phi0_d, u0_d);
+    return check_launch();
+}
+
+template <typename T, bool SH, int NP>
 static int two_pass(lb_ctx *c, int nsteps)
 {
     const auto p = make_coll<T>(c->p);
@@ -246,7 +261,7 @@ static int two_pass(lb_ctx *c, int nsteps)
     for (int t = 0; t < nsteps; t++) {
         const int a = c->buf.cur, b = 1 - a;
         k_phi_pull<T><<<grid, 256, 0, c->stream>>>((const T *)c->buf.g[a], (T *)c->phi, nx, ny, nz, c->S);
-        k_collide_pull<T, SH><<<grid, 256, 0, c->stream>>>((const T *)c->buf.f[a], (const T *)c->buf.g[a],
+        k_collide_pull<T, SH, NP><<<grid, 256, 0, c->stream>>>((const T *)c->buf.f[a], (const T *)c->buf.g[a],
                                                            (const T *)c->phi, (T *)c->buf.f[b],
                                                            (T *)c->buf.g[b], p, nx, ny, nz, c->S);
         int rc = check_launch();
@@ -267,9 +282,17 @@ int launch_two_pass_fp64_raw(const lb_params &prm, const double *fa, const doubl
     return check_launch();
 }
 
+template <typename T, bool SH>
+static int two_pass_t(lb_ctx *c, int nsteps)
+{
+    if (c->npts == 19) return two_pass<T, SH, 19>(c, nsteps);
+    if (c->npts == 27) return two_pass<T, SH, 27>(c, nsteps);
+    return two_pass<T, SH, 7>(c, nsteps);
+}
+
 int launch_step_two_pass(lb_ctx *c, int nsteps)
 {
-    return c->p.precision == LB_FP64 ? two_pass<double, false>(c, nsteps) : two_pass<float, true>(c, nsteps);
+    return c->p.precision == LB_FP64 ? two_pass_t<double, false>(c, nsteps) : two_pass_t<float, true>(c, nsteps);
 }
 
 int launch_moments(lb_ctx *c, double *rho, double *u, double *phi)

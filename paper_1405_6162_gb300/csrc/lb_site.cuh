@@ -29,17 +29,66 @@ struct Nbr {
     __device__ __forceinline__ int src(int i) const { return at(-cx(i), -cy(i), -cz(i)); }
 };
 
+// The phi stencil of NP points: 7 = nearest faces, d_a phi = (phi(x + e_a) -
+// phi(x - e_a))/2, lap phi = sum of the 6 faces - 6 phi(x); 19 / 27 =
+// the isotropic lattice-weighted differences over the D3Q19 / D3Q27
+// neighbourhoods, d_a phi = 3 sum_c W_c c_a phi(x + c) and
+// lap phi = 6 sum_c W_c (phi(x + c) - phi(x)), with W the D3Q19 weights
+// (1/18 faces, 1/36 edges) or the D3Q27 ones (2/27, 1/54, 1/216 corners).
+// Loads T, computes in R.
+template <int NP, typename R, typename T>
+__device__ __forceinline__ void stencil_np(const T *__restrict__ phi, const Nbr &n, R ph,
+                                           R &dx, R &dy, R &dz, R &lap)
+{
+    static_assert(NP == 7 || NP == 19 || NP == 27, "stencil of 7, 19 or 27 points");
+    if constexpr (NP == 7) {
+        const R xp = R(phi[n.at(1, 0, 0)]), xm = R(phi[n.at(-1, 0, 0)]);
+        const R yp = R(phi[n.at(0, 1, 0)]), ym = R(phi[n.at(0, -1, 0)]);
+        const R zp = R(phi[n.at(0, 0, 1)]), zm = R(phi[n.at(0, 0, -1)]);
+        dx = R(0.5) * (xp - xm);
+        dy = R(0.5) * (yp - ym);
+        dz = R(0.5) * (zp - zm);
+        lap = ((xp + xm) + (yp + ym)) + (zp + zm) - R(6) * ph;
+    } else {
+        // per weight class k (1 faces, 2 edges, 3 corners): sum of phi and the
+        // signed sums sum c_a phi
+        R sum[4] = {}, da[4] = {}, db[4] = {}, dc[4] = {};
+#pragma unroll
+        for (int a = -1; a <= 1; a++)
+#pragma unroll
+            for (int b = -1; b <= 1; b++)
+#pragma unroll
+                for (int c = -1; c <= 1; c++) {
+                    const int k = a * a + b * b + c * c;
+                    if (k == 0 || (NP == 19 && k == 3)) continue;
+                    const R v = R(phi[n.at(a, b, c)]);
+                    sum[k] += v;
+                    if (a) da[k] += a > 0 ? v : -v;
+                    if (b) db[k] += b > 0 ? v : -v;
+                    if (c) dc[k] += c > 0 ? v : -v;
+                }
+        if constexpr (NP == 19) {
+            const R gf = R(1.0 / 6.0), ge = R(1.0 / 12.0);
+            dx = gf * da[1] + ge * da[2];
+            dy = gf * db[1] + ge * db[2];
+            dz = gf * dc[1] + ge * dc[2];
+            lap = R(1.0 / 3.0) * sum[1] + R(1.0 / 6.0) * sum[2] - R(4) * ph;
+        } else {
+            const R gf = R(2.0 / 9.0), ge = R(1.0 / 18.0), gc = R(1.0 / 72.0);
+            dx = gf * da[1] + ge * da[2] + gc * da[3];
+            dy = gf * db[1] + ge * db[2] + gc * db[3];
+            dz = gf * dc[1] + ge * dc[2] + gc * dc[3];
+            lap = R(4.0 / 9.0) * sum[1] + R(1.0 / 9.0) * sum[2] + R(1.0 / 36.0) * sum[3] - R(38.0 / 9.0) * ph;
+        }
+    }
+}
+
+// the 7-point stencil in the storage type
 template <typename T>
 __device__ __forceinline__ void stencil(const T *__restrict__ phi, const Nbr &n, T ph,
                                         T &dx, T &dy, T &dz, T &lap)
 {
-    const T xp = phi[n.at(1, 0, 0)], xm = phi[n.at(-1, 0, 0)];
-    const T yp = phi[n.at(0, 1, 0)], ym = phi[n.at(0, -1, 0)];
-    const T zp = phi[n.at(0, 0, 1)], zm = phi[n.at(0, 0, -1)];
-    dx = T(0.5) * (xp - xm);
-    dy = T(0.5) * (yp - ym);
-    dz = T(0.5) * (zp - zm);
-    lap = ((xp + xm) + (yp + ym)) + (zp + zm) - T(6) * ph;
+    stencil_np<7, T>(phi, n, ph, dx, dy, dz, lap);
 }
 
 // phi = sum of the 19 pulled g values at the site of n (component stride S)
@@ -52,9 +101,9 @@ __device__ __forceinline__ T phi_site(const T *__restrict__ ga, const Nbr &n, lo
     return sum19(g);
 }
 
-// Pull f and g to site s, collide with the phi stencil, write the
+// Pull f and g to site s, collide with the NP-point phi stencil, write the
 // post-collision values at s.
-template <typename T, bool SH>
+template <typename T, bool SH, int NP = 7>
 __device__ __forceinline__ void collide_site(const T *__restrict__ fa, const T *__restrict__ ga,
                                              const T *__restrict__ phi, T *__restrict__ fb,
                                              T *__restrict__ gb, const Coll<T> &p, const Nbr &n, long long s,
@@ -69,7 +118,7 @@ __device__ __forceinline__ void collide_site(const T *__restrict__ fa, const T *
     }
     const T ph = phi[s];
     T dx, dy, dz, lap;
-    stencil(phi, n, ph, dx, dy, dz, lap);
+    stencil_np<NP, T>(phi, n, ph, dx, dy, dz, lap);
     collide<T, SH>(p, f, g, ph, dx, dy, dz, lap);
 #pragma unroll
     for (int i = 0; i < Q; i++) {

@@ -140,7 +140,7 @@ __device__ __forceinline__ Eq<T> load_eq(const T *__restrict__ g, long long S, l
     return make_eq(g[src], v[0], v[1], v[2], v[3]);
 }
 
-template <typename T, bool SH>
+template <typename T, bool SH, int NP>
 __global__ void __launch_bounds__(kT1Threads, sizeof(T) == 8 ? 2 : 3)
 k_t1_collide(const T *__restrict__ fa, T *__restrict__ ga /* level a: phi in, mu/u out */, T *__restrict__ fb,
              Coll<T> p, int nx, int ny, int nz, long long S)
@@ -155,7 +155,7 @@ k_t1_collide(const T *__restrict__ fa, T *__restrict__ ga /* level a: phi in, mu
     for (int i = 0; i < Q; i++) f[i] = fa[(size_t)i * S + n.src(i)];
     const T ph = phi[s];
     T dx, dy, dz, lap;
-    stencil(phi, n, ph, dx, dy, dz, lap);
+    stencil_np<NP, T>(phi, n, ph, dx, dy, dz, lap);
     // the general collision's f part; g's result is its equilibrium, kept as moments
     T ux, uy, uz, mu;
     collide_f<T, SH>(p, f, ph, dx, dy, dz, lap, ux, uy, uz, mu);
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(32 * kPhiWarps) k_t1_phi(const T *__restrict__
 // g state of the reduced form as post-streaming FP64 rows [i0, i1):
 // streamed equilibria of the previous step's moments (m_valid), else the
 // equilibrium at each site from phi(t), its stencil and u from f.
-template <typename T, bool SH>
+template <typename T, bool SH, int NP>
 __global__ void __launch_bounds__(kT1Threads) k_t1_g_state(const T *__restrict__ fa, const T *__restrict__ gcur,
                                                             const T *__restrict__ gprev, int m_valid, Coll<T> p,
                                                             double *__restrict__ out, int i0, int i1, int nx,
@@ -297,9 +297,8 @@ __global__ void __launch_bounds__(kT1Threads) k_t1_g_state(const T *__restrict__
     density_moments(f, R, jx, jy, jz);
     const double rho = SH ? double(p.rho0) + R : R;
     const double ph = double(gcur[s]);
-    const double xp = gcur[n.at(1, 0, 0)], xm = gcur[n.at(-1, 0, 0)], yp = gcur[n.at(0, 1, 0)];
-    const double ym = gcur[n.at(0, -1, 0)], zp = gcur[n.at(0, 0, 1)], zm = gcur[n.at(0, 0, -1)];
-    const double lap = ((xp + xm) + (yp + ym)) + (zp + zm) - 6.0 * ph;
+    double dx, dy, dz, lap;
+    stencil_np<NP, double>(gcur, n, ph, dx, dy, dz, lap);
     const double mu = ph * (double(p.A) + double(p.B) * ph * ph) - double(p.kappa) * lap;
     const Eq<double> e = make_eq(ph, gmh_of(ph, mu, double(p.gamma)), jx / rho, jy / rho, jz / rho);
 #pragma unroll
@@ -323,7 +322,7 @@ __global__ void __launch_bounds__(kT1Threads) k_t1_from_full(const T *__restrict
 
 // full-form g (post-collision storage) from the reduced form: A_i(x - c_i) =
 // the g state at x.  gcur is phi(t) (a copy: gout is the current level)
-template <typename T, bool SH>
+template <typename T, bool SH, int NP>
 __global__ void __launch_bounds__(kT1Threads) k_t1_to_full(const T *__restrict__ fa, const T *__restrict__ gcur,
                                                             const T *__restrict__ gprev, int m_valid, Coll<T> p,
                                                             T *__restrict__ gout, int nx, int ny, int nz, long long S)
@@ -339,9 +338,8 @@ __global__ void __launch_bounds__(kT1Threads) k_t1_to_full(const T *__restrict__
     density_moments(f, R, jx, jy, jz);
     const double rho = SH ? double(p.rho0) + R : R;
     const double ph = double(gcur[s]);
-    const double xp = gcur[n.at(1, 0, 0)], xm = gcur[n.at(-1, 0, 0)], yp = gcur[n.at(0, 1, 0)];
-    const double ym = gcur[n.at(0, -1, 0)], zp = gcur[n.at(0, 0, 1)], zm = gcur[n.at(0, 0, -1)];
-    const double lap = ((xp + xm) + (yp + ym)) + (zp + zm) - 6.0 * ph;
+    double dx, dy, dz, lap;
+    stencil_np<NP, double>(gcur, n, ph, dx, dy, dz, lap);
     const double mu = ph * (double(p.A) + double(p.B) * ph * ph) - double(p.kappa) * lap;
     const Eq<double> own = make_eq(ph, gmh_of(ph, mu, double(p.gamma)), jx / rho, jy / rho, jz / rho);
 #pragma unroll
@@ -365,7 +363,7 @@ __global__ void __launch_bounds__(kT1Threads) k_t1_copy_phi(const T *__restrict_
 
 inline unsigned grid_of(long long N) { return (unsigned)((N + kT1Threads - 1) / kT1Threads); }
 
-template <typename T, bool SH>
+template <typename T, bool SH, int NP>
 int run_t1(lb_ctx *c, int nsteps)
 {
     const auto p = make_coll<T>(c->p);
@@ -395,7 +393,7 @@ int run_t1(lb_ctx *c, int nsteps)
     const dim3 pblock(32, kPhiWarps);
     for (int t = 0; t < nsteps; t++) {
         const int a = c->buf.cur, b = 1 - a;
-        k_t1_collide<T, SH><<<grid, kT1Threads, 0, c->stream>>>((const T *)c->buf.f[a], (T *)c->buf.g[a],
+        k_t1_collide<T, SH, NP><<<grid, kT1Threads, 0, c->stream>>>((const T *)c->buf.f[a], (T *)c->buf.g[a],
                                                                 (T *)c->buf.f[b], p, nx, ny, nz, c->S);
         k_t1_phi<T, KY><<<pgrid, pblock, 0, c->stream>>>((const T *)c->buf.g[a], (T *)c->buf.g[b], nx, ny, nz, kzc,
                                                           c->S);
@@ -409,15 +407,64 @@ int run_t1(lb_ctx *c, int nsteps)
 
 }  // namespace
 
+template <typename T, bool SH>
+int run_t1_t(lb_ctx *c, int nsteps)
+{
+    if (c->npts == 19) return run_t1<T, SH, 19>(c, nsteps);
+    if (c->npts == 27) return run_t1<T, SH, 27>(c, nsteps);
+    return run_t1<T, SH, 7>(c, nsteps);
+}
+
+template <typename T, bool SH, int NP>
+void to_full(lb_ctx *c)
+{
+    const int cur = c->buf.cur, oth = 1 - cur;
+    k_t1_copy_phi<T><<<grid_of(c->N), kT1Threads, 0, c->stream>>>((const T *)c->buf.g[cur], (T *)c->phi, c->N);
+    k_t1_to_full<T, SH, NP><<<grid_of(c->N), kT1Threads, 0, c->stream>>>(
+        (const T *)c->buf.f[cur], (const T *)c->phi, (const T *)c->buf.g[oth], c->m_valid, make_coll<T>(c->p),
+        (T *)c->buf.g[cur], c->p.nx, c->p.ny, c->p.nz, c->S);
+}
+
+template <typename T, bool SH>
+void to_full_t(lb_ctx *c)
+{
+    if (c->npts == 19)
+        to_full<T, SH, 19>(c);
+    else if (c->npts == 27)
+        to_full<T, SH, 27>(c);
+    else
+        to_full<T, SH, 7>(c);
+}
+
+template <typename T, bool SH, int NP>
+void g_rows(lb_ctx *c, int i0, int i1, double *out)
+{
+    const int cur = c->buf.cur, oth = 1 - cur;
+    k_t1_g_state<T, SH, NP><<<grid_of(c->N), kT1Threads, 0, c->stream>>>(
+        (const T *)c->buf.f[cur], (const T *)c->buf.g[cur], (const T *)c->buf.g[oth], c->m_valid,
+        make_coll<T>(c->p), out, i0, i1, c->p.nx, c->p.ny, c->p.nz, c->S);
+}
+
+template <typename T, bool SH>
+void g_rows_t(lb_ctx *c, int i0, int i1, double *out)
+{
+    if (c->npts == 19)
+        g_rows<T, SH, 19>(c, i0, i1, out);
+    else if (c->npts == 27)
+        g_rows<T, SH, 27>(c, i0, i1, out);
+    else
+        g_rows<T, SH, 7>(c, i0, i1, out);
+}
+
 int launch_step_taug1(lb_ctx *c, int nsteps)
 {
-    return c->p.precision == LB_FP64 ? run_t1<double, false>(c, nsteps) : run_t1<float, true>(c, nsteps);
+    return c->p.precision == LB_FP64 ? run_t1_t<double, false>(c, nsteps) : run_t1_t<float, true>(c, nsteps);
 }
 
 // convert the stored state between the full and the reduced form
 int taug1_convert(lb_ctx *c, int to_reduced)
 {
-    const int cur = c->buf.cur, oth = 1 - cur;
+    const int cur = c->buf.cur;
     const unsigned grid = grid_of(c->N);
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
     if (to_reduced) {
@@ -439,19 +486,10 @@ int taug1_convert(lb_ctx *c, int to_reduced)
     // back to the full form: phi(t) into the phi scratch, then the 19 values
     // of g rebuilt into the current level (the previous step's moments are
     // read from the other level)
-    if (c->p.precision == LB_FP64) {
-        k_t1_copy_phi<double><<<grid, kT1Threads, 0, c->stream>>>((const double *)c->buf.g[cur], (double *)c->phi,
-                                                                  c->N);
-        k_t1_to_full<double, false><<<grid, kT1Threads, 0, c->stream>>>(
-            (const double *)c->buf.f[cur], (const double *)c->phi, (const double *)c->buf.g[oth], c->m_valid,
-            make_coll<double>(c->p), (double *)c->buf.g[cur], nx, ny, nz, c->S);
-    } else {
-        k_t1_copy_phi<float><<<grid, kT1Threads, 0, c->stream>>>((const float *)c->buf.g[cur], (float *)c->phi,
-                                                                 c->N);
-        k_t1_to_full<float, true><<<grid, kT1Threads, 0, c->stream>>>(
-            (const float *)c->buf.f[cur], (const float *)c->phi, (const float *)c->buf.g[oth], c->m_valid,
-            make_coll<float>(c->p), (float *)c->buf.g[cur], nx, ny, nz, c->S);
-    }
+    if (c->p.precision == LB_FP64)
+        to_full_t<double, false>(c);
+    else
+        to_full_t<float, true>(c);
     return check_launch();
 }
 
@@ -476,16 +514,10 @@ int taug1_phi_out(lb_ctx *c, double *out)
 
 int taug1_g_rows(lb_ctx *c, int i0, int i1, double *out)
 {
-    const int cur = c->buf.cur, oth = 1 - cur;
-    const unsigned grid = grid_of(c->N);
     if (c->p.precision == LB_FP64)
-        k_t1_g_state<double, false><<<grid, kT1Threads, 0, c->stream>>>(
-            (const double *)c->buf.f[cur], (const double *)c->buf.g[cur], (const double *)c->buf.g[oth], c->m_valid,
-            make_coll<double>(c->p), out, i0, i1, c->p.nx, c->p.ny, c->p.nz, c->S);
+        g_rows_t<double, false>(c, i0, i1, out);
     else
-        k_t1_g_state<float, true><<<grid, kT1Threads, 0, c->stream>>>(
-            (const float *)c->buf.f[cur], (const float *)c->buf.g[cur], (const float *)c->buf.g[oth], c->m_valid,
-            make_coll<float>(c->p), out, i0, i1, c->p.nx, c->p.ny, c->p.nz, c->S);
+        g_rows_t<float, true>(c, i0, i1, out);
     return check_launch();
 }
 

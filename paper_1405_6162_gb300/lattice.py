@@ -163,6 +163,10 @@ class Lattice:
         L.check(L.lib().lb_set_kernel(self.handle, KERNELS[kernel], block_x, block_y, z_chunk),
                 "lb_set_kernel")
 
+    def set_stencil(self, points: int = 7):
+        """Points of the phi stencils: 7 (nearest faces), 19 or 27 (isotropic)."""
+        L.check(L.lib().lb_set_stencil(self.handle, int(points)), "lb_set_stencil")
+
     def sync(self):
         """Wait for queued work; raises LBError(LB_ERR_TIMEOUT) if a bounded
         device-side wait gave up."""

@@ -63,6 +63,7 @@ def test_null_arguments(lib):
     assert lib.lb_moments(None, None, None, None, 0) == L.LB_ERR_INVALID
     assert lib.lb_reduce(None, None) == L.LB_ERR_INVALID
     assert lib.lb_set_kernel(None, 0, 0, 0, 0) == L.LB_ERR_INVALID
+    assert lib.lb_set_stencil(None, 19) == L.LB_ERR_INVALID
     lib.lb_destroy(None)
 
 
