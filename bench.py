@@ -305,11 +305,11 @@ def run_ours(args):
         results[prec] = dict(cfg=cfg, wall=wall, t_launch=t_launch, clocks=clk.summary(),
                              mass=float(r[0]))
 
-    # the tau_g = 1 reduced form on the same workload (the workload has tau_g = 1)
-    reduced = {}
-    for prec in ("fp32_shifted", "fp64"):
+    def timed(prec, kernel, npts):
+        """Whole-run and per-step times of `kernel` with the npts-point stencil."""
         with Lattice.from_params(DIMS, params, precision=prec) as lat:
-            lat.set_kernel("taug1")
+            lat.set_kernel(kernel)
+            lat.set_stencil(npts)
             lat.init(phi0)
             lat.step(args.warmup)
             barrier()
@@ -323,7 +323,12 @@ def run_ours(args):
                 barrier()
             wall = max_over_ranks(start.elapsed_time(stop) / 1e3)
             per = _time_steps(lat, max(5, min(k, 20)), torch)
-        reduced[prec] = dict(wall=wall, steps=k, t_launch=float(np.mean(per)), clocks=clk.summary())
+        return dict(wall=wall, steps=k, t_launch=float(np.mean(per)), clocks=clk.summary())
+
+    # the tau_g = 1 reduced form on the same workload (the workload has tau_g = 1)
+    reduced = {prec: timed(prec, "taug1", 7) for prec in ("fp32_shifted", "fp64")}
+    # the isotropic stencils on the default step
+    stencils = {(npts, prec): timed(prec, "auto", npts) for npts in (19, 27) for prec in ("fp32_shifted", "fp64")}
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     prec = "fp32_shifted"
@@ -394,6 +399,20 @@ def run_ours(args):
                              "peak_kind": f"{peak_kind} (copy bandwidth)",
                              "algorithmic_bytes_per_launch": bpl}}
 
+    def stencil_for(npts, prec):
+        r = stencils[(npts, prec)]
+        achieved = BYTES_PER_SITE[prec] * n / r["t_launch"] / 1e9
+        out = {"value": ws * n * r["steps"] / r["wall"] / 1e6, "unit": "MLUPS", "steps": r["steps"],
+               "ms_per_step": r["wall"] / r["steps"] * 1e3, "clocks": r["clocks"],
+               "hbm_frac": achieved / peak, "achieved_gbs": achieved}
+        if prec == "fp64":
+            fl = _profile_value("step_isotropic_stencils_256cubed", f"fp64_flops_per_site_{npts}")
+            pk = _profile_value("step_fp64_256cubed", "fp64_peak_tflops", need_current=False)
+            if fl and pk:
+                out["alu"] = {"achieved_tflops": fl * n / r["t_launch"] / 1e12, "peak_tflops": pk,
+                              "frac": fl * n / r["t_launch"] / 1e12 / pk, "flops_per_site": fl}
+        return out
+
     v32, roof32 = line_for("fp32_shifted")
     v64, roof64 = line_for("fp64")
     r32 = results["fp32_shifted"]
@@ -419,6 +438,10 @@ def run_ours(args):
         "taug1": {"what": "tau_g = 1 reduced form (LB_KERNEL_TAUG1): g kept as phi and (gmh, u), "
                           "same results as the general step to rounding; valid only at tau_g = 1",
                   "fp32_shifted": reduced_for("fp32_shifted"), "fp64": reduced_for("fp64")},
+        "stencils": {"what": "isotropic 19- / 27-point phi stencils (lb_set_stencil) on the default "
+                             "two-pass step; hbm_frac over the same 76-word algorithmic bytes",
+                     **{f"{npts}pt": {prec: stencil_for(npts, prec) for prec in ("fp32_shifted", "fp64")}
+                        for npts in (19, 27)}},
         "ensemble": ens,
         "adjoint": adj,
         "e2e": e2e,
@@ -472,6 +495,7 @@ def run_step_only(args):
         cfg = (args.kernel, *args.block)
     with Lattice.from_params(dims, params, precision=args.precision) as lat:
         lat.set_kernel(*cfg)
+        lat.set_stencil(args.stencil)
         lat.init(LI.spinodal_phi0(*dims, seed=1))
         lat.step(args.warmup)
         torch.cuda.synchronize()
@@ -480,6 +504,7 @@ def run_step_only(args):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
     print(json.dumps({"only": "step", "lattice": list(dims), "precision": args.precision, "launch": list(cfg),
+                      "stencil": args.stencil,
                       "steps": args.steps, "MLUPS": math.prod(dims) * args.steps / dt / 1e6}))
 
 
@@ -496,6 +521,8 @@ def main():
     ap.add_argument("--kernel", choices=["two_pass", "fused", "staged", "slab", "lag", "taug1"], default=None,
                     help="override the tuned launch of the --only lattice")
     ap.add_argument("--block", type=int, nargs=3, default=(0, 0, 0), metavar=("BX", "BY", "ZC"))
+    ap.add_argument("--stencil", type=int, choices=[7, 19, 27], default=7,
+                    help="points of the phi stencil of the --only lattice")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
