@@ -169,6 +169,21 @@ def step(dims, params, f, g, nsteps, kind="serial", npts=7):
     return f.reshape(19, n), g.reshape(19, n)
 
 
+def step_mrt(dims, params, f, g, nsteps, tau_bulk, tau_ghost, force=(0.0, 0.0, 0.0), kind="serial", npts=7):
+    """Advance (f, g) by ``nsteps`` with the multiple-relaxation-time
+    collision of f (shear rate 1/tau, bulk 1/tau_bulk, ghosts 1/tau_ghost)
+    and the Guo body force ``force``; returns new arrays."""
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    prm, pp = _prm(params, kind)
+    mrt, mp = _arr(np.array([tau_bulk, tau_ghost, *force], dtype=_dtype(kind)), kind)
+    f = np.array(f, dtype=_dtype(kind), copy=True).reshape(-1)
+    g = np.array(g, dtype=_dtype(kind), copy=True).reshape(-1)
+    _lib(kind).orc_step_mrt(nx, ny, nz, _npts(npts), pp, mp, f.ctypes.data_as(ctypes.c_void_p),
+                            g.ctypes.data_as(ctypes.c_void_p), int(nsteps))
+    return f.reshape(19, n), g.reshape(19, n)
+
+
 def moments(dims, f, g, kind="serial"):
     """(rho [N], u [3][N], phi [N])."""
     nx, ny, nz = dims

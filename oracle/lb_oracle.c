@@ -287,6 +287,110 @@ void orc_step(int nx, int ny, int nz, const real *prm, real *f, real *g, int nst
     orc_step_n(nx, ny, nz, 7, prm, f, g, nsteps);
 }
 
+/* Multiple-relaxation-time collision of f with a Guo body force.
+ *
+ * The collision is defined by projections, so that it does not depend on a
+ * choice of moment basis.  With m0 = sum h, m1 = sum h c, m2 = sum h c c, the
+ * second-order Hermite part of a vector h is
+ *   H(h)_i = w_i [m0 + c_i.m1/cs2 + Q_i:(m2 - m0 cs2 I)/(2 cs2^2)]
+ * and its ghost part is h - H(h) (the 9 directions of D3Q19 orthogonal to
+ * 1, c and c c).  At each site, with body force F (force density):
+ *   rho = sum f, j = sum f c, u = (j + F/2)/rho, feq = feq(rho, rho u, ...),
+ *   N = sum (f - feq) c c, split into its bulk part (tr N/3) I and the
+ *       traceless shear part; G = u F + F u split the same way;
+ *   X = (1 - w_s) N_shear + (1 - w_b) N_bulk
+ *     + (1 - w_s/2) G_shear + (1 - w_b/2) G_bulk,
+ *   f*_i = feq_i + w_i [c_i.F/(2 cs2) + Q_i:X/(2 cs2^2)]
+ *        + (1 - w_gh) ghost(f - feq)_i,
+ * with w_s = 1/tau (shear), w_b = 1/tau_bulk, w_gh = 1/tau_ghost.  The
+ * momentum after collision is j + F; with all three rates equal and F = 0
+ * this is the BGK collision of orc_step.  g relaxes by BGK (tau_g) toward
+ * geq evaluated with the same u.  mrt[] = {tau_bulk, tau_ghost, Fx, Fy, Fz}.
+ */
+void orc_step_mrt(int nx, int ny, int nz, int npts, const real *prm, const real *mrt, real *f, real *g,
+                  int nsteps)
+{
+    velocity_set();
+    const double cs2 = 1.0 / 3.0;
+    long N = (long)nx * ny * nz;
+    real *phi = malloc(sizeof(real) * N);
+    real *grad = malloc(sizeof(real) * 3 * N);
+    real *lap = malloc(sizeof(real) * N);
+    real *fs = malloc(sizeof(real) * NV * N);
+    real *gs = malloc(sizeof(real) * NV * N);
+    const real ws = 1.0 / prm[P_TAU], wb = 1.0 / mrt[0], wgh = 1.0 / mrt[1];
+    const real F[3] = {mrt[2], mrt[3], mrt[4]};
+    for (int t = 0; t < nsteps; t++) {
+        for (long s = 0; s < N; s++) {
+            real acc = 0.0;
+            for (int i = 0; i < NV; i++) acc += g[i * N + s];
+            phi[s] = acc;
+        }
+        orc_gradients_n(nx, ny, nz, npts, phi, grad, lap);
+#pragma omp parallel for
+        for (long s = 0; s < N; s++) {
+            real rho = 0.0, j[3] = {0.0, 0.0, 0.0}, u[3], ju[3], d[3], feq[NV], geq[NV], h[NV];
+            for (int i = 0; i < NV; i++) {
+                rho += f[i * N + s];
+                for (int a = 0; a < 3; a++) j[a] += f[i * N + s] * cv[i][a];
+            }
+            for (int a = 0; a < 3; a++) {
+                u[a] = (j[a] + 0.5 * F[a]) / rho;
+                ju[a] = rho * u[a];
+                d[a] = grad[a * N + s];
+            }
+            orc_site_equilibrium(prm, rho, ju, phi[s], d, lap[s], feq, geq);
+            /* moments of h = f - feq */
+            real m0 = 0.0, m1[3] = {0.0, 0.0, 0.0}, m2[3][3] = {{0.0}};
+            for (int i = 0; i < NV; i++) {
+                h[i] = f[i * N + s] - feq[i];
+                m0 += h[i];
+                for (int a = 0; a < 3; a++) {
+                    m1[a] += h[i] * cv[i][a];
+                    for (int b = 0; b < 3; b++) m2[a][b] += h[i] * cv[i][a] * cv[i][b];
+                }
+            }
+            real trN = (m2[0][0] + m2[1][1] + m2[2][2]) / 3.0;
+            real G[3][3], X[3][3], trG = 2.0 * (u[0] * F[0] + u[1] * F[1] + u[2] * F[2]) / 3.0;
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) {
+                    G[a][b] = u[a] * F[b] + F[a] * u[b];
+                    real nb = (a == b) ? trN : 0.0, gb = (a == b) ? trG : 0.0;
+                    X[a][b] = (1.0 - ws) * (m2[a][b] - nb) + (1.0 - wb) * nb
+                              + (1.0 - 0.5 * ws) * (G[a][b] - gb) + (1.0 - 0.5 * wb) * gb;
+                }
+            for (int i = 0; i < NV; i++) {
+                real hm1 = 0.0, cF = 0.0, qN = 0.0, qX = 0.0;
+                for (int a = 0; a < 3; a++) {
+                    hm1 += cv[i][a] * m1[a];
+                    cF += cv[i][a] * F[a];
+                    for (int b = 0; b < 3; b++) {
+                        double Q = cv[i][a] * cv[i][b] - (a == b ? cs2 : 0.0);
+                        qN += Q * (m2[a][b] - (a == b ? m0 * cs2 : 0.0));
+                        qX += Q * X[a][b];
+                    }
+                }
+                real herm = wv[i] * (m0 + hm1 / cs2 + qN / (2.0 * cs2 * cs2));
+                real ghost = h[i] - herm;
+                fs[i * N + s] = feq[i] + wv[i] * (cF / (2.0 * cs2) + qX / (2.0 * cs2 * cs2)) + (1.0 - wgh) * ghost;
+                gs[i * N + s] = g[i * N + s] - (g[i * N + s] - geq[i]) / prm[P_TAUG];
+            }
+        }
+#pragma omp parallel for
+        for (int z = 0; z < nz; z++)
+            for (int y = 0; y < ny; y++)
+                for (int x = 0; x < nx; x++) {
+                    long s = site(x, y, z, nx, ny, nz);
+                    for (int i = 0; i < NV; i++) {
+                        long dst = site(x + cv[i][0], y + cv[i][1], z + cv[i][2], nx, ny, nz);
+                        f[i * N + dst] = fs[i * N + s];
+                        g[i * N + dst] = gs[i * N + s];
+                    }
+                }
+    }
+    free(phi); free(grad); free(lap); free(fs); free(gs);
+}
+
 /* rho = sum f, u = sum f c / rho (SoA [3][N]), phi = sum g. */
 void orc_moments(int nx, int ny, int nz, const real *f, const real *g,
                  real *rho, real *u, real *phi)
