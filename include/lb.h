@@ -83,8 +83,15 @@ enum {
     LB_KERNEL_LAG = 5,      /* single pass, lagged pipeline: the CTA with
                                ticket c computes phi of site block c and
                                collides block c - D; bounded waits            */
-    LB_KERNEL_TAUG1 = 6     /* tau_g = 1 only: g kept as (phi, mu, u), whose
-                               equilibria it is exactly; ~49 words per site   */
+    LB_KERNEL_TAUG1 = 6     /* tau_g = 1 only: g kept as phi and (gmh, u),
+                               whose equilibria it is exactly; 49 words/site  */
+};
+
+/* Collision of f, lb_set_collision(). */
+enum {
+    LB_COLLISION_BGK = 0,   /* single relaxation time tau (default)            */
+    LB_COLLISION_MRT = 1    /* shear stress at 1/tau, bulk stress at
+                               1/tau_bulk, the 9 ghost modes at 1/tau_ghost    */
 };
 
 typedef struct lb_ctx lb_ctx;
@@ -204,6 +211,31 @@ int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk);
  * Paper: the "standard finite-difference" order-parameter update, Sec. II.A
  * (which names no stencil). */
 int lb_set_stencil(lb_ctx *c, int points);
+
+/* Collision of f used by later lb_step calls: LB_COLLISION_BGK (tau_bulk and
+ * tau_ghost ignored) or LB_COLLISION_MRT, the multiple-relaxation-time
+ * collision defined by projections onto the second-order Hermite space of
+ * D3Q19: with N = sum (f - feq) c c split into bulk ((tr N/3) I) and
+ * traceless shear parts, the shear part relaxes at 1/tau (shear viscosity
+ * (tau - 1/2)/3), the bulk part at 1/tau_bulk (bulk viscosity
+ * (2/9)(tau_bulk - 1/2)) and the 9 ghost directions (orthogonal to 1, c and
+ * c c) at 1/tau_ghost; with all three equal it is BGK.  g keeps its BGK
+ * collision (tau_g).  Requires tau_bulk, tau_ghost > 1/2, a kernel that is
+ * LB_KERNEL_AUTO or LB_KERNEL_TWO_PASS (others, now or in a later
+ * lb_set_kernel, give LB_ERR_INVALID), not an ensemble member; lb_adjoint_*
+ * refuse MRT contexts.  Paper: the "binary collision" kernel's collision
+ * operator, Sec. IV (BGK is its form; MRT is Ludwig's other). */
+int lb_set_collision(lb_ctx *c, int model, double tau_bulk, double tau_ghost);
+
+/* Uniform body force density F applied by Guo's scheme from the next
+ * lb_step: u = (sum f c + F/2)/rho enters the equilibria and lb_moments'
+ * velocity, the momentum of every site grows by F per step, and the
+ * second-order force terms relax with (1 - w/2) of the shear and bulk rates
+ * (with BGK, of 1/tau).  lb_reduce's momentum is sum f c (without F/2).
+ * (0, 0, 0) switches it off.  Same kernel, ensemble and adjoint limits as
+ * LB_COLLISION_MRT.  Paper: no counterpart (a NEXT extension of the
+ * collision). */
+int lb_set_force(lb_ctx *c, double fx, double fy, double fz);
 
 /* Synchronise the context's stream; returns LB_ERR_TIMEOUT if a bounded
  * device-side wait (the lagged kernel's inter-CTA waits) gave up since the

@@ -24,6 +24,8 @@ LB_FP64 = 0
 LB_FP32_SHIFTED = 1
 LB_HOST = 0
 LB_DEVICE = 1
+LB_COLLISION_BGK = 0
+LB_COLLISION_MRT = 1
 
 LB_KERNEL_AUTO = 0
 LB_KERNEL_TWO_PASS = 1
@@ -61,6 +63,8 @@ SIGNATURES = {
     "lb_set_state": (_I, [_P, _P, _P, _I]),
     "lb_set_kernel": (_I, [_P, _I, _I, _I, _I]),
     "lb_set_stencil": (_I, [_P, _I]),
+    "lb_set_collision": (_I, [_P, _I, ctypes.c_double, ctypes.c_double]),
+    "lb_set_force": (_I, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "lb_get_info": (_I, [_P, _P, _P, _P, _P]),
     "lb_sync": (_I, [_P]),
     "lb_set_wait_timeout": (_I, [_P, ctypes.c_longlong]),

@@ -209,15 +209,12 @@ __device__ __forceinline__ void collide_f(const Coll<T>& p, T (&f)[Q], T phi, T 
 #undef LBK_EDGES
 }
 
-// In-place BGK collision of f (collide_f) and of g at one site.
-template <typename T, bool SH>
-__device__ __forceinline__ void collide(const Coll<T>& p, T (&f)[Q], T (&g)[Q],
-                                        T phi, T dx, T dy, T dz, T lap)
+// In-place BGK collision of g at one site with velocity u and chemical
+// potential mu.
+template <typename T>
+__device__ __forceinline__ void collide_g(const Coll<T>& p, T (&g)[Q], T phi, T ux, T uy, T uz, T mu)
 {
     const T third = T(1.0 / 3.0), h = T(4.5);
-    T ux, uy, uz, mu;
-    collide_f<T, SH>(p, f, phi, dx, dy, dz, lap, ux, uy, uz, mu);
-
     // ---- g: omega_g geq_i = omega_g w_i [phi + 3 phi c.u + 9/2 (phi (c.u)^2 - phi u^2/3 + (Gamma mu - phi/3)(c^2 - 1))]
     const T cg = p.cg;
     const T px = phi * ux, py = phi * uy, pz = phi * uz;
@@ -250,6 +247,122 @@ __device__ __forceinline__ void collide(const Coll<T>& p, T (&f)[Q], T (&g)[Q],
     LBK_GEDGE(15, 16, py + pz, uy + uz)
     LBK_GEDGE(17, 18, py - pz, uy - uz)
 #undef LBK_GEDGE
+}
+
+// In-place BGK collision of f (collide_f) and of g at one site.
+template <typename T, bool SH>
+__device__ __forceinline__ void collide(const Coll<T>& p, T (&f)[Q], T (&g)[Q],
+                                        T phi, T dx, T dy, T dz, T lap)
+{
+    T ux, uy, uz, mu;
+    collide_f<T, SH>(p, f, phi, dx, dy, dz, lap, ux, uy, uz, mu);
+    collide_g<T>(p, g, phi, ux, uy, uz, mu);
+}
+
+// Rates and body force of the multiple-relaxation-time collision, with the
+// combinations the kernel uses formed on the host (in double, rounded once).
+template <typename T>
+struct Mrt {
+    T cs, cb;          // 1 - w_s, 1 - w_b          (w_s = 1/tau, w_b = 1/tau_bulk)
+    T hs, hb;          // 1 - w_s/2, 1 - w_b/2      (Guo's factors)
+    T og, cgh, kf;     // w_gh, 1 - w_gh, (2 - w_gh)/2   (w_gh = 1/tau_ghost)
+    T Fx, Fy, Fz;      // body force density
+    T hFx, hFy, hFz;   // F/2
+};
+
+// In-place multiple-relaxation-time collision of f with a Guo body force,
+// then the BGK collision of g with the force-corrected velocity
+// u = (j + F/2)/rho.  With N = sum (f - feq) c c (= Pi - R/3 I - S in the
+// shifted form), G = u F + F u, each split into bulk (trace/3 I) and shear
+// (traceless) parts,
+//   X  = (1 - w_s) N_s + (1 - w_b) N_b + (1 - w_s/2) G_s + (1 - w_b/2) G_b,
+// and the ghost part of f - feq relaxed at w_gh, the post-collision value is
+//   f*_i = (1 - w_gh) f_i + w_i [R' + 3 c_i.J' + 9/2 Q_i:S'],
+//   R' = w_gh R,  J' = w_gh rho u + (2 - w_gh)/2 F,
+//   S' = w_gh S + X - (1 - w_gh) N,
+// which is BGK when the three rates are equal and F = 0.
+template <typename T, bool SH>
+__device__ __forceinline__ void collide_mrt(const Coll<T>& p, const Mrt<T>& m, T (&f)[Q], T (&g)[Q],
+                                            T phi, T dx, T dy, T dz, T lap)
+{
+    T R, jx, jy, jz;
+    density_moments(f, R, jx, jy, jz);
+    const T third = T(1.0 / 3.0), h = T(4.5);
+    const T rho = SH ? p.rho0 + R : R;
+    const T rinv = T(1) / rho;
+    const T Jx = jx + m.hFx, Jy = jy + m.hFy, Jz = jz + m.hFz;   // rho u
+    const T ux = Jx * rinv, uy = Jy * rinv, uz = Jz * rinv;
+    const T phi2 = phi * phi;
+    const T mu = phi * (p.A + p.B * phi2) - p.kappa * lap;
+    const T pb = phi2 * (T(0.5) * p.A + T(0.75) * p.B * phi2)
+               - p.kappa * (phi * lap + T(0.5) * (dx * dx + dy * dy + dz * dz));
+    // S = P + rho u u
+    const T Sxx = pb + p.kappa * dx * dx + Jx * ux;
+    const T Syy = pb + p.kappa * dy * dy + Jy * uy;
+    const T Szz = pb + p.kappa * dz * dz + Jz * uz;
+    const T Sxy = p.kappa * dx * dy + Jx * uy;
+    const T Sxz = p.kappa * dx * dz + Jx * uz;
+    const T Syz = p.kappa * dy * dz + Jy * uz;
+    // second moment of the stored values (sum f c c)
+    const T e7 = f[7] + f[8], e9 = f[9] + f[10], e11 = f[11] + f[12], e13 = f[13] + f[14];
+    const T e15 = f[15] + f[16], e17 = f[17] + f[18];
+    const T Pxx = (f[1] + f[2]) + (e7 + e9) + (e11 + e13);
+    const T Pyy = (f[3] + f[4]) + (e7 + e9) + (e15 + e17);
+    const T Pzz = (f[5] + f[6]) + (e11 + e13) + (e15 + e17);
+    const T Pxy = e7 - e9, Pxz = e11 - e13, Pyz = e15 - e17;
+    // N = Pi - R/3 I - S, bulk part nb, shear part N - nb I
+    const T R3 = R * third;
+    const T Nxx = Pxx - R3 - Sxx, Nyy = Pyy - R3 - Syy, Nzz = Pzz - R3 - Szz;
+    const T Nxy = Pxy - Sxy, Nxz = Pxz - Sxz, Nyz = Pyz - Syz;
+    const T nb = (Nxx + Nyy + Nzz) * third;
+    // G = u F + F u, bulk part gb
+    const T Gxx = T(2) * ux * m.Fx, Gyy = T(2) * uy * m.Fy, Gzz = T(2) * uz * m.Fz;
+    const T Gxy = ux * m.Fy + uy * m.Fx, Gxz = ux * m.Fz + uz * m.Fx, Gyz = uy * m.Fz + uz * m.Fy;
+    const T gb = (Gxx + Gyy + Gzz) * third;
+    // S' = w_gh S + X - (1 - w_gh) N; X's bulk terms act on the trace only
+    const T xb = m.cb * nb + m.hb * gb - (m.cs * nb + m.hs * gb);   // bulk minus shear rate, times I
+    const T a = m.cs - m.cgh;                                       // N's net shear coefficient
+    const T Spxx = m.og * Sxx + a * Nxx + m.hs * Gxx + xb;
+    const T Spyy = m.og * Syy + a * Nyy + m.hs * Gyy + xb;
+    const T Spzz = m.og * Szz + a * Nzz + m.hs * Gzz + xb;
+    const T Spxy = m.og * Sxy + a * Nxy + m.hs * Gxy;
+    const T Spxz = m.og * Sxz + a * Nxz + m.hs * Gxz;
+    const T Spyz = m.og * Syz + a * Nyz + m.hs * Gyz;
+    const T t3 = (Spxx + Spyy + Spzz) * third;
+    const T Rp = m.og * R;
+    const T Jpx = m.og * Jx + m.kf * m.Fx, Jpy = m.og * Jy + m.kf * m.Fy, Jpz = m.og * Jz + m.kf * m.Fz;
+
+    const T cf = m.cgh;
+    const T w0 = T(1.0 / 3.0), w1 = T(1.0 / 18.0), w2 = T(1.0 / 36.0);
+    const T b = Rp - h * t3;
+    f[0] = cf * f[0] + w0 * b;
+    const T B1 = w1 * b, B2 = w2 * b;
+    const T f1h = w1 * h, f1t = w1 * T(3), f2h = w2 * h, f2t = w2 * T(3);
+#define LBK_MFACE(IP, IM, SAA, JA)                                 \
+    {                                                              \
+        const T s_ = f1h * SAA + B1, a_ = f1t * JA;                \
+        f[IP] = cf * f[IP] + (s_ + a_);                            \
+        f[IM] = cf * f[IM] + (s_ - a_);                            \
+    }
+    LBK_MFACE(1, 2, Spxx, Jpx)
+    LBK_MFACE(3, 4, Spyy, Jpy)
+    LBK_MFACE(5, 6, Spzz, Jpz)
+#undef LBK_MFACE
+#define LBK_MEDGES(IP, IM, KP, KM, SAA, SBB, SAB, JA, JB)            \
+    {                                                                \
+        const T e_ = f2h * (SAA + SBB) + B2, o_ = f1h * SAB;         \
+        const T sp = e_ + o_, sm = e_ - o_;                          \
+        const T ap = f2t * (JA + JB), am = f2t * (JA - JB);          \
+        f[IP] = cf * f[IP] + (sp + ap);                              \
+        f[IM] = cf * f[IM] + (sp - ap);                              \
+        f[KP] = cf * f[KP] + (sm + am);                              \
+        f[KM] = cf * f[KM] + (sm - am);                              \
+    }
+    LBK_MEDGES(7, 8, 9, 10, Spxx, Spyy, Spxy, Jpx, Jpy)
+    LBK_MEDGES(11, 12, 13, 14, Spxx, Spzz, Spxz, Jpx, Jpz)
+    LBK_MEDGES(15, 16, 17, 18, Spyy, Spzz, Spyz, Jpy, Jpz)
+#undef LBK_MEDGES
+    collide_g<T>(p, g, phi, ux, uy, uz, mu);
 }
 
 }  // namespace lbk

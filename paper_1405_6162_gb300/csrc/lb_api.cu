@@ -247,8 +247,8 @@ static int ensure_adj(lb_ctx *c)
 int lb_adjoint_step(lb_ctx *c, const double *f, const double *g, const double *af_in, const double *ag_in,
                     double *af_out, double *ag_out, double *dkappa)
 {
-    if (!c || c->p.precision != LB_FP64 || c->npts != 7 || !f || !g || !af_in || !ag_in || !af_out || !ag_out ||
-        !dkappa)
+    if (!c || c->p.precision != LB_FP64 || c->npts != 7 || lbk::uses_mrt(c) || !f || !g || !af_in || !ag_in ||
+        !af_out || !ag_out || !dkappa)
         return LB_ERR_INVALID;
     if (af_out == af_in || ag_out == ag_in || af_out == ag_in || ag_out == af_in) return LB_ERR_INVALID;
     const int rc = ensure_adj(c);
@@ -259,7 +259,8 @@ int lb_adjoint_step(lb_ctx *c, const double *f, const double *g, const double *a
 int lb_adjoint_init(lb_ctx *c, const double *phi0, const double *u0, const double *af0, const double *ag0,
                     double *phi0_bar, double *dkappa)
 {
-    if (!c || c->p.precision != LB_FP64 || c->npts != 7 || !phi0 || !af0 || !ag0 || !phi0_bar || !dkappa)
+    if (!c || c->p.precision != LB_FP64 || c->npts != 7 || lbk::uses_mrt(c) || !phi0 || !af0 || !ag0 ||
+        !phi0_bar || !dkappa)
         return LB_ERR_INVALID;
     const int rc = ensure_adj(c);
     if (rc) return rc;
@@ -334,6 +335,33 @@ static bool seven_point_only(int kernel)
            kernel == LB_KERNEL_LAG;
 }
 
+static bool any_force(const double *F) { return F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0; }
+
+int lb_set_collision(lb_ctx *c, int model, double tau_bulk, double tau_ghost)
+{
+    if (!c || c->batch_owned) return LB_ERR_INVALID;
+    if (model != LB_COLLISION_BGK && model != LB_COLLISION_MRT) return LB_ERR_INVALID;
+    if (model == LB_COLLISION_MRT) {
+        if (!(tau_bulk > 0.5) || !(tau_ghost > 0.5) || !std::isfinite(tau_bulk) || !std::isfinite(tau_ghost))
+            return LB_ERR_INVALID;
+        if (c->kernel != LB_KERNEL_AUTO && c->kernel != LB_KERNEL_TWO_PASS) return LB_ERR_INVALID;
+        c->tau_bulk = tau_bulk;
+        c->tau_ghost = tau_ghost;
+    }
+    c->collision = model;
+    return LB_OK;
+}
+
+int lb_set_force(lb_ctx *c, double fx, double fy, double fz)
+{
+    if (!c || c->batch_owned) return LB_ERR_INVALID;
+    if (!std::isfinite(fx) || !std::isfinite(fy) || !std::isfinite(fz)) return LB_ERR_INVALID;
+    const double F[3] = {fx, fy, fz};
+    if (any_force(F) && c->kernel != LB_KERNEL_AUTO && c->kernel != LB_KERNEL_TWO_PASS) return LB_ERR_INVALID;
+    for (int a = 0; a < 3; a++) c->force[a] = F[a];
+    return LB_OK;
+}
+
 int lb_set_stencil(lb_ctx *c, int points)
 {
     if (!c || c->batch_owned) return LB_ERR_INVALID;
@@ -349,6 +377,7 @@ int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk)
     if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_TAUG1 || c->batch_owned) return LB_ERR_INVALID;
     if (block_x < 0 || block_y < 0 || z_chunk < 0) return LB_ERR_INVALID;
     if (c->npts != 7 && seven_point_only(kernel)) return LB_ERR_INVALID;
+    if (lbk::uses_mrt(c) && kernel != LB_KERNEL_AUTO && kernel != LB_KERNEL_TWO_PASS) return LB_ERR_INVALID;
     if (kernel == LB_KERNEL_STAGED) {
         int rc = lbk::staged_validate(c->p.precision, block_x, block_y, z_chunk);
         if (rc) return rc;

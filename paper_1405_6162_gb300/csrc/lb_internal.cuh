@@ -49,6 +49,9 @@ struct lb_ctx {
     int reduced = 0;      // tau_g = 1 form: g kept as phi and (gmh, u), see lb_taug1.cu
     int m_valid = 0;      // reduced form: the previous step's (gmh, u) are present
     int npts = 7;         // points of the phi stencil: 7, 19 or 27 (lb_set_stencil)
+    int collision = LB_COLLISION_BGK;       // collision of f (lb_set_collision)
+    double tau_bulk = 1.0, tau_ghost = 1.0; // MRT relaxation times
+    double force[3] = {0.0, 0.0, 0.0};      // Guo body force density (lb_set_force)
     int kernel = LB_KERNEL_AUTO;
     int block_x = 0, block_y = 0, z_chunk = 0;
     lb_alloc_fn alloc = nullptr;
@@ -57,6 +60,37 @@ struct lb_ctx {
 };
 
 namespace lbk {
+
+// the f collision needs the MRT / forced kernel
+inline bool uses_mrt(const lb_ctx *c)
+{
+    return c->collision == LB_COLLISION_MRT || c->force[0] != 0.0 || c->force[1] != 0.0 || c->force[2] != 0.0;
+}
+
+// MRT rates and force in the arithmetic type T; BGK with a force uses the
+// shear rate for all three rates (Guo's BGK scheme)
+template <typename T>
+inline Mrt<T> make_mrt(const lb_ctx *c)
+{
+    const double ws = 1.0 / c->p.tau;
+    const bool mrt = c->collision == LB_COLLISION_MRT;
+    const double wb = mrt ? 1.0 / c->tau_bulk : ws, wg = mrt ? 1.0 / c->tau_ghost : ws;
+    Mrt<T> m;
+    m.cs = T(1.0 - ws);
+    m.cb = T(1.0 - wb);
+    m.hs = T(1.0 - 0.5 * ws);
+    m.hb = T(1.0 - 0.5 * wb);
+    m.og = T(wg);
+    m.cgh = T(1.0 - wg);
+    m.kf = T(1.0 - 0.5 * wg);
+    m.Fx = T(c->force[0]);
+    m.Fy = T(c->force[1]);
+    m.Fz = T(c->force[2]);
+    m.hFx = T(0.5 * c->force[0]);
+    m.hFy = T(0.5 * c->force[1]);
+    m.hFz = T(0.5 * c->force[2]);
+    return m;
+}
 
 constexpr int kLagBlock = 256;       // sites per block of the lagged kernel
 constexpr long long kLagSlack = 128;  // extra lag (blocks) beyond the stencil reach

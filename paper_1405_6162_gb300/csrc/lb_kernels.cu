@@ -79,13 +79,42 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? LBK_K2_MINB64 : LBK_K2_M
     collide_site<T, SH, NP>(fa, ga, phi, fb, gb, p, n, s, S);
 }
 
+// multiple-relaxation-time collision of f with a Guo body force (collide_mrt)
+template <typename T, bool SH, int NP>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? LBK_K2_MINB64 : LBK_K2_MINB32)
+k_collide_pull_mrt(const T *__restrict__ fa, const T *__restrict__ ga, const T *__restrict__ phi,
+                   T *__restrict__ fb, T *__restrict__ gb, Coll<T> p, Mrt<T> m, int nx, int ny, int nz,
+                   long long S)
+{
+    const long long N = (long long)nx * ny * nz;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const Nbr n(s, nx, ny, nz);
+    T f[Q], g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const size_t o = (size_t)i * S + n.src(i);
+        f[i] = fa[o];
+        g[i] = ga[o];
+    }
+    const T ph = phi[s];
+    T dx, dy, dz, lap;
+    stencil_np<NP, T>(phi, n, ph, dx, dy, dz, lap);
+    collide_mrt<T, SH>(p, m, f, g, ph, dx, dy, dz, lap);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        fb[(size_t)i * S + s] = f[i];
+        gb[(size_t)i * S + s] = g[i];
+    }
+}
+
 // ------------------------------------------------------------------ moments / state
 
 template <typename T, bool SH>
 __global__ void __launch_bounds__(256) k_moments(const T *__restrict__ fa, const T *__restrict__ ga,
                                                  double *__restrict__ rho, double *__restrict__ u,
-                                                 double *__restrict__ phi, double rho0,
-                                                 int nx, int ny, int nz, long long S)
+                                                 double *__restrict__ phi, double rho0, double hFx,
+                                                 double hFy, double hFz, int nx, int ny, int nz, long long S)
 {
     const long long N = (long long)nx * ny * nz;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -103,9 +132,9 @@ __global__ void __launch_bounds__(256) k_moments(const T *__restrict__ fa, const
     const double r = SH ? rho0 + R : R;
     if (rho) rho[s] = r;
     if (u) {
-        u[s] = jx / r;
-        u[N + s] = jy / r;
-        u[2 * N + s] = jz / r;
+        u[s] = (jx + hFx) / r;   // u = (sum f c + F/2) / rho
+        u[N + s] = (jy + hFy) / r;
+        u[2 * N + s] = (jz + hFz) / r;
     }
     if (phi) phi[s] = sum19(g);
 }
@@ -256,14 +285,21 @@ template <typename T, bool SH, int NP>
 static int two_pass(lb_ctx *c, int nsteps)
 {
     const auto p = make_coll<T>(c->p);
+    const bool mrt = uses_mrt(c);
+    const auto m = make_mrt<T>(c);
     const unsigned grid = grid_for(c->N, 256);
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
     for (int t = 0; t < nsteps; t++) {
         const int a = c->buf.cur, b = 1 - a;
-        k_phi_pull<T><<<grid, 256, 0, c->stream>>>((const T *)c->buf.g[a], (T *)c->phi, nx, ny, nz, c->S);
-        k_collide_pull<T, SH, NP><<<grid, 256, 0, c->stream>>>((const T *)c->buf.f[a], (const T *)c->buf.g[a],
-                                                           (const T *)c->phi, (T *)c->buf.f[b],
-                                                           (T *)c->buf.g[b], p, nx, ny, nz, c->S);
+        const T *fa = (const T *)c->buf.f[a], *ga = (const T *)c->buf.g[a];
+        T *fb = (T *)c->buf.f[b], *gb = (T *)c->buf.g[b];
+        k_phi_pull<T><<<grid, 256, 0, c->stream>>>(ga, (T *)c->phi, nx, ny, nz, c->S);
+        if (mrt)
+            k_collide_pull_mrt<T, SH, NP><<<grid, 256, 0, c->stream>>>(fa, ga, (const T *)c->phi, fb, gb, p, m, nx,
+                                                                     ny, nz, c->S);
+        else
+            k_collide_pull<T, SH, NP><<<grid, 256, 0, c->stream>>>(fa, ga, (const T *)c->phi, fb, gb, p, nx, ny,
+                                                                 nz, c->S);
         int rc = check_launch();
         if (rc) return rc;
         c->buf.cur = b;
@@ -298,15 +334,18 @@ int launch_step_two_pass(lb_ctx *c, int nsteps)
 int launch_moments(lb_ctx *c, double *rho, double *u, double *phi)
 {
     const int cur = c->buf.cur;
+    const double hF[3] = {0.5 * c->force[0], 0.5 * c->force[1], 0.5 * c->force[2]};
     const unsigned grid = grid_for(c->N, 256);
     if (c->p.precision == LB_FP64)
         k_moments<double, false><<<grid, 256, 0, c->stream>>>((const double *)c->buf.f[cur],
                                                               (const double *)c->buf.g[cur], rho, u, phi,
-                                                              c->p.rho0, c->p.nx, c->p.ny, c->p.nz, c->S);
+                                                              c->p.rho0, hF[0], hF[1], hF[2], c->p.nx,
+                                                              c->p.ny, c->p.nz, c->S);
     else
         k_moments<float, true><<<grid, 256, 0, c->stream>>>((const float *)c->buf.f[cur],
                                                             (const float *)c->buf.g[cur], rho, u, phi,
-                                                            c->p.rho0, c->p.nx, c->p.ny, c->p.nz, c->S);
+                                                            c->p.rho0, hF[0], hF[1], hF[2], c->p.nx,
+                                                            c->p.ny, c->p.nz, c->S);
     return check_launch();
 }
 

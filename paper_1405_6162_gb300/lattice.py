@@ -167,6 +167,17 @@ class Lattice:
         """Points of the phi stencils: 7 (nearest faces), 19 or 27 (isotropic)."""
         L.check(L.lib().lb_set_stencil(self.handle, int(points)), "lb_set_stencil")
 
+    def set_collision(self, model: str = "bgk", tau_bulk: float = 1.0, tau_ghost: float = 1.0):
+        """Collision of f: "bgk", or "mrt" with the bulk and ghost relaxation
+        times (shear: the lattice's tau)."""
+        code = {"bgk": L.LB_COLLISION_BGK, "mrt": L.LB_COLLISION_MRT}[model]
+        L.check(L.lib().lb_set_collision(self.handle, code, float(tau_bulk), float(tau_ghost)),
+                "lb_set_collision")
+
+    def set_force(self, fx: float = 0.0, fy: float = 0.0, fz: float = 0.0):
+        """Uniform body force density (Guo's scheme); zero switches it off."""
+        L.check(L.lib().lb_set_force(self.handle, float(fx), float(fy), float(fz)), "lb_set_force")
+
     def sync(self):
         """Wait for queued work; raises LBError(LB_ERR_TIMEOUT) if a bounded
         device-side wait gave up."""

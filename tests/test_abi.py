@@ -64,6 +64,8 @@ def test_null_arguments(lib):
     assert lib.lb_reduce(None, None) == L.LB_ERR_INVALID
     assert lib.lb_set_kernel(None, 0, 0, 0, 0) == L.LB_ERR_INVALID
     assert lib.lb_set_stencil(None, 19) == L.LB_ERR_INVALID
+    assert lib.lb_set_collision(None, L.LB_COLLISION_MRT, 1.0, 1.0) == L.LB_ERR_INVALID
+    assert lib.lb_set_force(None, 0.0, 0.0, 1e-5) == L.LB_ERR_INVALID
     lib.lb_destroy(None)
 
 
