@@ -41,6 +41,7 @@ METRIC = "MLUPS and % of HBM roofline (fused step), FP32-shifted vs FP64 at stat
 ORACLE_SAMPLE = (64, 64, 64)
 ORACLE_STEPS = 30
 E2E_STEPS = 50
+MRT_RATES = (1.3, 0.6)      # tau_bulk, tau_ghost of the MRT measurement
 FALLBACK_HBM = 6800.0
 # kernels one timestep launches, per lb_set_kernel choice
 STEP_KERNELS = {"auto": "timestep = k_phi_pull + k_collide_pull (two launches)",
@@ -305,11 +306,14 @@ def run_ours(args):
         results[prec] = dict(cfg=cfg, wall=wall, t_launch=t_launch, clocks=clk.summary(),
                              mass=float(r[0]))
 
-    def timed(prec, kernel, npts):
-        """Whole-run and per-step times of `kernel` with the npts-point stencil."""
+    def timed(prec, kernel, npts, mrt=None):
+        """Whole-run and per-step times of `kernel` with the npts-point stencil
+        (and the MRT collision with (tau_bulk, tau_ghost) = mrt)."""
         with Lattice.from_params(DIMS, params, precision=prec) as lat:
             lat.set_kernel(kernel)
             lat.set_stencil(npts)
+            if mrt:
+                lat.set_collision("mrt", *mrt)
             lat.init(phi0)
             lat.step(args.warmup)
             barrier()
@@ -327,6 +331,8 @@ def run_ours(args):
 
     # the tau_g = 1 reduced form on the same workload (the workload has tau_g = 1)
     reduced = {prec: timed(prec, "taug1", 7) for prec in ("fp32_shifted", "fp64")}
+    # the MRT collision of f on the default step
+    mrt = {prec: timed(prec, "auto", 7, MRT_RATES) for prec in ("fp32_shifted", "fp64")}
     # the isotropic stencils on the default step
     stencils = {(npts, prec): timed(prec, "auto", npts) for npts in (19, 27) for prec in ("fp32_shifted", "fp64")}
 
@@ -413,6 +419,20 @@ def run_ours(args):
                               "frac": fl * n / r["t_launch"] / 1e12 / pk, "flops_per_site": fl}
         return out
 
+    def mrt_for(prec):
+        r = mrt[prec]
+        achieved = BYTES_PER_SITE[prec] * n / r["t_launch"] / 1e9
+        out = {"value": ws * n * r["steps"] / r["wall"] / 1e6, "unit": "MLUPS", "steps": r["steps"],
+               "ms_per_step": r["wall"] / r["steps"] * 1e3, "clocks": r["clocks"],
+               "hbm_frac": achieved / peak, "achieved_gbs": achieved}
+        if prec == "fp64":
+            fl = _profile_value("step_mrt_256cubed", "fp64_flops_per_site")
+            pk = _profile_value("step_fp64_256cubed", "fp64_peak_tflops", need_current=False)
+            if fl and pk:
+                out["alu"] = {"achieved_tflops": fl * n / r["t_launch"] / 1e12, "peak_tflops": pk,
+                              "frac": fl * n / r["t_launch"] / 1e12 / pk, "flops_per_site": fl}
+        return out
+
     v32, roof32 = line_for("fp32_shifted")
     v64, roof64 = line_for("fp64")
     r32 = results["fp32_shifted"]
@@ -438,6 +458,9 @@ def run_ours(args):
         "taug1": {"what": "tau_g = 1 reduced form (LB_KERNEL_TAUG1): g kept as phi and (gmh, u), "
                           "same results as the general step to rounding; valid only at tau_g = 1",
                   "fp32_shifted": reduced_for("fp32_shifted"), "fp64": reduced_for("fp64")},
+        "mrt": {"what": f"multiple-relaxation-time collision of f (lb_set_collision), tau = 1, "
+                        f"tau_bulk = {MRT_RATES[0]}, tau_ghost = {MRT_RATES[1]}, on the default two-pass step",
+                "fp32_shifted": mrt_for("fp32_shifted"), "fp64": mrt_for("fp64")},
         "stencils": {"what": "isotropic 19- / 27-point phi stencils (lb_set_stencil) on the default "
                              "two-pass step; hbm_frac over the same 76-word algorithmic bytes",
                      **{f"{npts}pt": {prec: stencil_for(npts, prec) for prec in ("fp32_shifted", "fp64")}
@@ -496,6 +519,8 @@ def run_step_only(args):
     with Lattice.from_params(dims, params, precision=args.precision) as lat:
         lat.set_kernel(*cfg)
         lat.set_stencil(args.stencil)
+        if args.mrt:
+            lat.set_collision("mrt", *args.mrt)
         lat.init(LI.spinodal_phi0(*dims, seed=1))
         lat.step(args.warmup)
         torch.cuda.synchronize()
@@ -523,6 +548,8 @@ def main():
     ap.add_argument("--block", type=int, nargs=3, default=(0, 0, 0), metavar=("BX", "BY", "ZC"))
     ap.add_argument("--stencil", type=int, choices=[7, 19, 27], default=7,
                     help="points of the phi stencil of the --only lattice")
+    ap.add_argument("--mrt", type=float, nargs=2, default=None, metavar=("TAU_BULK", "TAU_GHOST"),
+                    help="MRT collision of the --only lattice")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
