@@ -269,3 +269,22 @@ def trajectory_loss(dims, params, phi0, phi_target, nsteps, kind="serial"):
     f, g = step(dims, params, f, g, nsteps, kind=kind)
     phi_t = g.sum(0)
     return np.sum((phi_t - phi_target) ** 2)
+
+
+def select_sites(x, mask):
+    """The values of x (last axis: sites in site order) at the sites whose
+    mask byte is non-zero, in site order -- the masked copy-out of the
+    paper's copyFromTargetMasked (Sec. III.B)."""
+    x = np.asarray(x)
+    keep = np.asarray(mask).reshape(-1) != 0
+    return x[..., keep]
+
+
+def scatter_sites(x, mask, values):
+    """A copy of x with ``values`` (last axis: the selected sites in site
+    order) written at the sites whose mask byte is non-zero -- the masked
+    copy-in of copyToTargetMasked (Sec. III.B)."""
+    out = np.array(x, copy=True)
+    keep = np.asarray(mask).reshape(-1) != 0
+    out[..., keep] = values
+    return out
