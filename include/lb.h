@@ -181,6 +181,27 @@ int lb_reduce(lb_ctx *c, double out[5]);
 int lb_get_state(lb_ctx *c, double *f, double *g, int ptr_kind);
 int lb_set_state(lb_ctx *c, const double *f, const double *g, int ptr_kind);
 
+/* Masked copy-out: the moments (as lb_moments) of the sites whose mask byte
+ * is non-zero, compacted in site order: rho[count], u[3][count] (row stride
+ * count), phi[count].  mask is unsigned char[N] in ptr_kind memory, as are
+ * the outputs, which must hold at least count values per row (N always
+ * suffices); any output may be NULL.  *count (host, may be NULL) receives
+ * the number of selected sites.  Synchronises the stream (the count is read
+ * back).  Works in every kernel form.  Errors: LB_ERR_INVALID, LB_ERR_NOMEM,
+ * LB_ERR_CUDA.  Paper: copyFromTargetMasked, Sec. III.B (a stream compaction
+ * on the GPU). */
+int lb_moments_masked(lb_ctx *c, const unsigned char *mask, double *rho, double *u, double *phi,
+                      long long *count, int ptr_kind);
+
+/* Masked state I/O: the post-streaming f, g (as lb_get_state) of the
+ * selected sites as double[19][count] each (row stride count), and the
+ * inverse, which overwrites only the selected sites.  Refused
+ * (LB_ERR_INVALID) in the tau_g = 1 reduced form.  Synchronise the stream.
+ * Paper: copyFromTargetMasked / copyToTargetMasked, Sec. III.B. */
+int lb_get_state_masked(lb_ctx *c, const unsigned char *mask, double *f, double *g, long long *count,
+                        int ptr_kind);
+int lb_set_state_masked(lb_ctx *c, const unsigned char *mask, const double *f, const double *g, int ptr_kind);
+
 /* Select the step kernel (LB_KERNEL_*) and its launch shape: block_x x
  * block_y threads per CTA and z_chunk planes per CTA of the fused, staged
  * and slab kernels (0 = library default for any of the three).  For

@@ -63,6 +63,9 @@ SIGNATURES = {
     "lb_set_state": (_I, [_P, _P, _P, _I]),
     "lb_set_kernel": (_I, [_P, _I, _I, _I, _I]),
     "lb_set_stencil": (_I, [_P, _I]),
+    "lb_moments_masked": (_I, [_P, _P, _P, _P, _P, _P, _I]),
+    "lb_get_state_masked": (_I, [_P, _P, _P, _P, _P, _I]),
+    "lb_set_state_masked": (_I, [_P, _P, _P, _P, _I]),
     "lb_set_collision": (_I, [_P, _I, ctypes.c_double, ctypes.c_double]),
     "lb_set_force": (_I, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "lb_get_info": (_I, [_P, _P, _P, _P, _P]),

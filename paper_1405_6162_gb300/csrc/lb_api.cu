@@ -60,6 +60,10 @@ void free_all(lb_ctx *c)
     dev_free(c, c->dev_out, 8 * sizeof(double));
     dev_free(c, c->lag_counters, (size_t)(c->p.nz + 1) * sizeof(unsigned long long));
     if (!c->batch_owned) dev_free(c, c->err_flag, sizeof(unsigned int));
+    dev_free(c, c->mask_buf, (size_t)c->N);
+    dev_free(c, c->mask_scratch, lbk::masked_scratch_ints(c->N) * sizeof(int));
+    c->mask_buf = nullptr;
+    c->mask_scratch = nullptr;
     dev_free(c, c->adj, 6 * (size_t)c->N * sizeof(double));
     dev_free(c, c->adj_part, (size_t)lbk::adjoint_blocks(c->N) * sizeof(double));
     c->adj = nullptr;
@@ -496,6 +500,110 @@ int lb_set_state(lb_ctx *c, const double *f, const double *g, int ptr_kind)
     if (!rc && c->reduced && g) rc = lbk::taug1_convert(c, 1);
     if (!rc) rc = sync(c);
     return rc;
+}
+
+// Device mask and the compaction offsets of the selected sites; *total
+// receives their number (synchronises the stream).
+static int masked_prepare(lb_ctx *c, const unsigned char *mask, int ptr_kind, const unsigned char **mask_d,
+                          long long *total)
+{
+    if (!c->mask_scratch) c->mask_scratch = (int *)dev_alloc(c, lbk::masked_scratch_ints(c->N) * sizeof(int));
+    if (!c->mask_scratch) return LB_ERR_NOMEM;
+    int rc = LB_OK;
+    if (ptr_kind == LB_HOST) {
+        if (!c->mask_buf) c->mask_buf = (unsigned char *)dev_alloc(c, (size_t)c->N);
+        if (!c->mask_buf) return LB_ERR_NOMEM;
+        rc = copy(c, c->mask_buf, mask, (size_t)c->N, cudaMemcpyHostToDevice);
+        *mask_d = c->mask_buf;
+    } else {
+        *mask_d = mask;
+    }
+    if (!rc) rc = lbk::launch_mask_scan(c, *mask_d, c->mask_scratch);
+    int tot = 0;
+    if (!rc) rc = copy(c, &tot, c->mask_scratch + lbk::masked_total_offset(c->N), sizeof(int), cudaMemcpyDeviceToHost);
+    if (!rc) rc = sync(c);
+    *total = tot;
+    return rc;
+}
+
+int lb_moments_masked(lb_ctx *c, const unsigned char *mask, double *rho, double *u, double *phi, long long *count,
+                      int ptr_kind)
+{
+    if (!c || !mask || (ptr_kind != LB_HOST && ptr_kind != LB_DEVICE)) return LB_ERR_INVALID;
+    const unsigned char *mask_d = nullptr;
+    long long total = 0;
+    int rc = masked_prepare(c, mask, ptr_kind, &mask_d, &total);
+    if (rc) return rc;
+    if (count) *count = total;
+    if (total == 0 || (!rho && !u && !phi)) return LB_OK;
+    if (ptr_kind == LB_DEVICE) return lbk::launch_masked_moments(c, mask_d, c->mask_scratch, rho, u, phi);
+    rc = ensure_io(c);
+    if (rc) return rc;
+    const size_t nb = (size_t)total * sizeof(double);
+    // rho and u through the staging buffer (4 total values), then phi
+    if (rho || u) {
+        rc = lbk::launch_masked_moments(c, mask_d, c->mask_scratch, c->io, c->io + total, nullptr);
+        if (!rc && rho) rc = copy(c, rho, c->io, nb, cudaMemcpyDeviceToHost);
+        if (!rc && u) rc = copy(c, u, c->io + total, 3 * nb, cudaMemcpyDeviceToHost);
+        if (!rc) rc = sync(c);
+    }
+    if (!rc && phi) {
+        rc = lbk::launch_masked_moments(c, mask_d, c->mask_scratch, nullptr, nullptr, c->io);
+        if (!rc) rc = copy(c, phi, c->io, nb, cudaMemcpyDeviceToHost);
+        if (!rc) rc = sync(c);
+    }
+    return rc;
+}
+
+// rows of f (which = 0) or g (1) between the lattice and [19][total] arrays
+static int masked_state(lb_ctx *c, const unsigned char *mask, double *f, double *g, const double *fin,
+                        const double *gin, long long *count, int ptr_kind, int to_device_state)
+{
+    if (!c || !mask || (ptr_kind != LB_HOST && ptr_kind != LB_DEVICE) || c->reduced) return LB_ERR_INVALID;
+    const unsigned char *mask_d = nullptr;
+    long long total = 0;
+    int rc = masked_prepare(c, mask, ptr_kind, &mask_d, &total);
+    if (rc) return rc;
+    if (count) *count = total;
+    if (total == 0) return LB_OK;
+    double *out[2] = {f, g};
+    const double *in[2] = {fin, gin};
+    if (ptr_kind == LB_DEVICE) {
+        for (int which = 0; which < 2 && !rc; which++) {
+            double *buf = to_device_state ? const_cast<double *>(in[which]) : out[which];
+            if (buf) rc = lbk::launch_masked_rows(c, mask_d, c->mask_scratch, which, 0, lbk::Q, buf, to_device_state);
+        }
+        return rc;
+    }
+    rc = ensure_io(c);
+    if (rc) return rc;
+    const size_t T = (size_t)total;
+    for (int which = 0; which < 2 && !rc; which++) {
+        if (to_device_state ? !in[which] : !out[which]) continue;
+        for (int i0 = 0; i0 < lbk::Q && !rc; i0 += 4) {   // 4 rows of total values fit the 4N staging buffer
+            const int i1 = i0 + 4 < lbk::Q ? i0 + 4 : lbk::Q;
+            const size_t bytes = (size_t)(i1 - i0) * T * sizeof(double);
+            if (to_device_state) {
+                rc = copy(c, c->io, in[which] + (size_t)i0 * T, bytes, cudaMemcpyHostToDevice);
+                if (!rc) rc = lbk::launch_masked_rows(c, mask_d, c->mask_scratch, which, i0, i1, c->io, 1);
+            } else {
+                rc = lbk::launch_masked_rows(c, mask_d, c->mask_scratch, which, i0, i1, c->io, 0);
+                if (!rc) rc = copy(c, out[which] + (size_t)i0 * T, c->io, bytes, cudaMemcpyDeviceToHost);
+            }
+            if (!rc) rc = sync(c);
+        }
+    }
+    return rc;
+}
+
+int lb_get_state_masked(lb_ctx *c, const unsigned char *mask, double *f, double *g, long long *count, int ptr_kind)
+{
+    return masked_state(c, mask, f, g, nullptr, nullptr, count, ptr_kind, 0);
+}
+
+int lb_set_state_masked(lb_ctx *c, const unsigned char *mask, const double *f, const double *g, int ptr_kind)
+{
+    return masked_state(c, mask, nullptr, nullptr, f, g, nullptr, ptr_kind, 1);
 }
 
 }  // extern "C"

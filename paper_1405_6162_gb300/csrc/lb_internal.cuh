@@ -52,6 +52,8 @@ struct lb_ctx {
     int collision = LB_COLLISION_BGK;       // collision of f (lb_set_collision)
     double tau_bulk = 1.0, tau_ghost = 1.0; // MRT relaxation times
     double force[3] = {0.0, 0.0, 0.0};      // Guo body force density (lb_set_force)
+    unsigned char *mask_buf = nullptr;      // [N] device copy of a host mask (lazy)
+    int *mask_scratch = nullptr;            // compaction counts and offsets (lazy)
     int kernel = LB_KERNEL_AUTO;
     int block_x = 0, block_y = 0, z_chunk = 0;
     lb_alloc_fn alloc = nullptr;
@@ -164,6 +166,15 @@ int launch_step_taug1(lb_ctx *c, int nsteps);
 int taug1_convert(lb_ctx *c, int to_reduced);
 int taug1_g_rows(lb_ctx *c, int i0, int i1, double *out);
 int taug1_phi_out(lb_ctx *c, double *out);
+
+// masked copies (lb_masked.cu)
+size_t masked_scratch_ints(long long N);
+int masked_total_offset(long long N);
+int launch_mask_scan(lb_ctx *c, const unsigned char *mask_d, int *scratch);
+int launch_masked_moments(lb_ctx *c, const unsigned char *mask_d, const int *scratch, double *rho, double *u,
+                          double *phi);
+int launch_masked_rows(lb_ctx *c, const unsigned char *mask_d, const int *scratch, int which, int i0, int i1,
+                       double *io, int to_device_state);
 
 // lagged kernel (lb_lag.cu)
 int launch_step_lag(lb_ctx *c, int nsteps);

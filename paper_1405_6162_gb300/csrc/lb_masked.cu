@@ -1,0 +1,250 @@
+// lb_masked.cu -- masked copies between the lattice and compact arrays: the
+// sites whose mask byte is non-zero, in site order (targetDP Sec. III.B,
+// copyFromTargetMasked / copyToTargetMasked).
+//
+// A stream compaction in three launches: per-CTA counts of selected sites
+// (one site per thread, __syncthreads_count), one CTA's exclusive scan of the
+// counts (offsets[nb] = total), then the gather or scatter kernel, whose
+// threads find their compact index from the CTA offset, the warp prefix of
+// the warps before them and a ballot within their warp.  The order is the
+// site order, so the result is unique and bit-exact.
+#include <cuda_runtime.h>
+
+#include "d3q19.cuh"
+#include "lb_internal.cuh"
+#include "lb_site.cuh"
+
+namespace lbk {
+
+namespace {
+
+constexpr int kMaskThreads = 512;               // sites per CTA, one per thread
+constexpr int kMaskWarps = kMaskThreads / 32;
+constexpr unsigned kFull = 0xffffffffu;
+static_assert(kMaskThreads % 32 == 0 && kMaskWarps <= 32, "CTA of whole warps, at most 32");
+
+__global__ void __launch_bounds__(kMaskThreads) k_mask_count(const unsigned char *__restrict__ mask, long long N,
+                                                             int *__restrict__ counts)
+{
+    const long long s = (long long)blockIdx.x * kMaskThreads + threadIdx.x;
+    const int c = __syncthreads_count(s < N && mask[s] != 0);
+    if (threadIdx.x == 0) counts[blockIdx.x] = c;
+}
+
+// inclusive scan over a warp
+__device__ __forceinline__ int warp_incl(int x)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// offsets[i] = counts[0] + ... + counts[i - 1] for i < nb, offsets[nb] = total
+__global__ void __launch_bounds__(kMaskThreads) k_mask_scan(const int *__restrict__ counts, int nb,
+                                                            int *__restrict__ offsets)
+{
+    __shared__ int warp_tot[32];
+    __shared__ int carry_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += kMaskThreads) {
+        const int i = base + threadIdx.x;
+        const int v = i < nb ? counts[i] : 0;
+        const int x = warp_incl(v);
+        if (lane == 31) warp_tot[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            const int t = warp_incl(lane < kMaskWarps ? warp_tot[lane] : 0);
+            if (lane < kMaskWarps) warp_tot[lane] = t;
+        }
+        __syncthreads();
+        const int carry = carry_s;
+        if (i < nb) offsets[i] = carry + (warp ? warp_tot[warp - 1] : 0) + x - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry_s = carry + warp_tot[kMaskWarps - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) offsets[nb] = carry_s;
+}
+
+// compact index of this thread's site among the selected ones (all threads
+// of the CTA must call it)
+__device__ __forceinline__ int compact_index(bool flag, const int *__restrict__ offsets)
+{
+    __shared__ int warp_pre[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(kFull, flag);
+    const int before = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) warp_pre[warp] = __popc(bal);
+    __syncthreads();
+    if (warp == 0) {
+        const int v = lane < kMaskWarps ? warp_pre[lane] : 0;
+        const int t = warp_incl(v) - v;
+        if (lane < kMaskWarps) warp_pre[lane] = t;
+    }
+    __syncthreads();
+    return offsets[blockIdx.x] + warp_pre[warp] + before;
+}
+
+// rho, u = (sum f c + F/2)/rho, phi of the selected sites; u as [3][total].
+// REDUCED: phi is component 0 of the g level (the tau_g = 1 form).
+template <typename T, bool SH, bool REDUCED>
+__global__ void __launch_bounds__(kMaskThreads) k_masked_moments(
+    const T *__restrict__ fa, const T *__restrict__ ga, const unsigned char *__restrict__ mask,
+    const int *__restrict__ offsets, int nb, double rho0, double hFx, double hFy, double hFz,
+    double *__restrict__ rho, double *__restrict__ u, double *__restrict__ phi, int nx, int ny, int nz, long long S)
+{
+    const long long N = (long long)nx * ny * nz;
+    const long long s = (long long)blockIdx.x * kMaskThreads + threadIdx.x;
+    const bool flag = s < N && mask[s] != 0;
+    const int dst = compact_index(flag, offsets);
+    if (!flag) return;
+    const long long total = offsets[nb];
+    const Nbr n((int)s, nx, ny, nz);
+    double f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) f[i] = double(fa[(size_t)i * S + n.src(i)]);
+    double R, jx, jy, jz;
+    density_moments(f, R, jx, jy, jz);
+    const double r = SH ? rho0 + R : R;
+    if (rho) rho[dst] = r;
+    if (u) {
+        u[dst] = (jx + hFx) / r;
+        u[total + dst] = (jy + hFy) / r;
+        u[2 * total + dst] = (jz + hFz) / r;
+    }
+    if (phi) {
+        if (REDUCED) {
+            phi[dst] = double(ga[s]);
+        } else {
+            double g[Q];
+#pragma unroll
+            for (int i = 0; i < Q; i++) g[i] = double(ga[(size_t)i * S + n.src(i)]);
+            phi[dst] = sum19(g);
+        }
+    }
+}
+
+// rows [i0, i1) of the post-streaming state A_i(x - c_i) + w_i shift at the
+// selected sites, out[(i - i0) * total + k]
+template <typename T>
+__global__ void __launch_bounds__(kMaskThreads) k_masked_get(const T *__restrict__ a,
+                                                             const unsigned char *__restrict__ mask,
+                                                             const int *__restrict__ offsets, int nb, int i0, int i1,
+                                                             double shift, double *__restrict__ out, int nx, int ny,
+                                                             int nz, long long S)
+{
+    const long long N = (long long)nx * ny * nz;
+    const long long s = (long long)blockIdx.x * kMaskThreads + threadIdx.x;
+    const bool flag = s < N && mask[s] != 0;
+    const int dst = compact_index(flag, offsets);
+    if (!flag) return;
+    const long long total = offsets[nb];
+    const Nbr n((int)s, nx, ny, nz);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        if (i < i0 || i >= i1) continue;
+        out[(size_t)(i - i0) * total + dst] = double(a[(size_t)i * S + n.src(i)]) + weight(i) * shift;
+    }
+}
+
+// the inverse: A_i(x - c_i) = in[(i - i0) * total + k] - w_i shift at the
+// selected sites
+template <typename T>
+__global__ void __launch_bounds__(kMaskThreads) k_masked_set(T *__restrict__ a, const unsigned char *__restrict__ mask,
+                                                             const int *__restrict__ offsets, int nb, int i0, int i1,
+                                                             double shift, const double *__restrict__ in, int nx,
+                                                             int ny, int nz, long long S)
+{
+    const long long N = (long long)nx * ny * nz;
+    const long long s = (long long)blockIdx.x * kMaskThreads + threadIdx.x;
+    const bool flag = s < N && mask[s] != 0;
+    const int dst = compact_index(flag, offsets);
+    if (!flag) return;
+    const long long total = offsets[nb];
+    const Nbr n((int)s, nx, ny, nz);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        if (i < i0 || i >= i1) continue;
+        a[(size_t)i * S + n.src(i)] = T(in[(size_t)(i - i0) * total + dst] - weight(i) * shift);
+    }
+}
+
+inline int mask_blocks(long long N) { return (int)((N + kMaskThreads - 1) / kMaskThreads); }
+
+}  // namespace
+
+size_t masked_scratch_ints(long long N) { return 2 * (size_t)mask_blocks(N) + 1; }
+
+// counts and offsets of the selected sites (scratch: masked_scratch_ints ints)
+int launch_mask_scan(lb_ctx *c, const unsigned char *mask_d, int *scratch)
+{
+    const int nb = mask_blocks(c->N);
+    int *counts = scratch, *offsets = scratch + nb;
+    k_mask_count<<<nb, kMaskThreads, 0, c->stream>>>(mask_d, c->N, counts);
+    k_mask_scan<<<1, kMaskThreads, 0, c->stream>>>(counts, nb, offsets);
+    return check_launch();
+}
+
+int masked_total_offset(long long N) { return 2 * mask_blocks(N); }   // index of offsets[nb] in the scratch
+
+int launch_masked_moments(lb_ctx *c, const unsigned char *mask_d, const int *scratch, double *rho, double *u,
+                          double *phi)
+{
+    const int nb = mask_blocks(c->N);
+    const int *offsets = scratch + nb;
+    const int cur = c->buf.cur;
+    const double hF[3] = {0.5 * c->force[0], 0.5 * c->force[1], 0.5 * c->force[2]};
+    const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+#define LBK_MM(T, SH, RED)                                                                                      \
+    k_masked_moments<T, SH, RED><<<nb, kMaskThreads, 0, c->stream>>>(                                          \
+        (const T *)c->buf.f[cur], (const T *)c->buf.g[cur], mask_d, offsets, nb, c->p.rho0, hF[0], hF[1], hF[2], \
+        rho, u, phi, nx, ny, nz, c->S)
+    if (c->p.precision == LB_FP64) {
+        if (c->reduced)
+            LBK_MM(double, false, true);
+        else
+            LBK_MM(double, false, false);
+    } else {
+        if (c->reduced)
+            LBK_MM(float, true, true);
+        else
+            LBK_MM(float, true, false);
+    }
+#undef LBK_MM
+    return check_launch();
+}
+
+int launch_masked_rows(lb_ctx *c, const unsigned char *mask_d, const int *scratch, int which, int i0, int i1,
+                       double *io, int to_device_state)
+{
+    const int nb = mask_blocks(c->N);
+    const int *offsets = scratch + nb;
+    const int cur = c->buf.cur;
+    const double shift = (which == 0 && c->p.precision == LB_FP32_SHIFTED) ? c->p.rho0 : 0.0;
+    void *a = which == 0 ? c->buf.f[cur] : c->buf.g[cur];
+    const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    if (c->p.precision == LB_FP64) {
+        if (to_device_state)
+            k_masked_set<double><<<nb, kMaskThreads, 0, c->stream>>>((double *)a, mask_d, offsets, nb, i0, i1, shift,
+                                                                     io, nx, ny, nz, c->S);
+        else
+            k_masked_get<double><<<nb, kMaskThreads, 0, c->stream>>>((const double *)a, mask_d, offsets, nb, i0, i1,
+                                                                     shift, io, nx, ny, nz, c->S);
+    } else {
+        if (to_device_state)
+            k_masked_set<float><<<nb, kMaskThreads, 0, c->stream>>>((float *)a, mask_d, offsets, nb, i0, i1, shift, io,
+                                                                    nx, ny, nz, c->S);
+        else
+            k_masked_get<float><<<nb, kMaskThreads, 0, c->stream>>>((const float *)a, mask_d, offsets, nb, i0, i1,
+                                                                    shift, io, nx, ny, nz, c->S);
+    }
+    return check_launch();
+}
+
+}  // namespace lbk

@@ -232,6 +232,77 @@ class Lattice:
             raise ValueError("f and g must both be host or both be device arrays")
         L.check(L.lib().lb_set_state(self.handle, fp, gp, fk), "lb_set_state")
 
+    # -------------------------------------------------------------- masked copies
+    def _mask(self, mask):
+        """(pointer, kind, keepalive) of a uint8 mask of N sites: numpy (host)
+        or a CUDA torch tensor (device)."""
+        if isinstance(mask, np.ndarray):
+            m = np.ascontiguousarray(mask.reshape(-1), dtype=np.uint8)
+            if m.size != self.N:
+                raise ValueError(f"mask has {m.size} sites, the lattice {self.N}")
+            return m.ctypes.data, L.LB_HOST, m
+        torch = _torch()
+        if torch.is_tensor(mask) and mask.is_cuda:
+            m = mask.reshape(-1).to(torch.uint8).contiguous()
+            if m.numel() != self.N:
+                raise ValueError(f"mask has {m.numel()} sites, the lattice {self.N}")
+            return m.data_ptr(), L.LB_DEVICE, m
+        raise TypeError("mask must be a numpy array or a CUDA torch tensor")
+
+    def count_masked(self, mask) -> int:
+        """Number of sites whose mask byte is non-zero."""
+        mp, kind, keep = self._mask(mask)
+        cnt = ctypes.c_longlong(0)
+        L.check(L.lib().lb_moments_masked(self.handle, mp, None, None, None, ctypes.byref(cnt), kind),
+                "lb_moments_masked")
+        return int(cnt.value)
+
+    def moments_masked(self, mask):
+        """(rho [k], u [3,k], phi [k]) of the k selected sites in site order;
+        numpy for a numpy mask, CUDA tensors for a CUDA mask."""
+        mp, kind, keep = self._mask(mask)
+        k = self.count_masked(mask)
+        cnt = ctypes.c_longlong(0)
+        if kind == L.LB_DEVICE:
+            torch = _torch()
+            rho, u, phi = (torch.empty(m * max(k, 1), dtype=torch.float64, device="cuda") for m in (1, 3, 1))
+            L.check(L.lib().lb_moments_masked(self.handle, mp, rho.data_ptr(), u.data_ptr(), phi.data_ptr(),
+                                              ctypes.byref(cnt), kind), "lb_moments_masked")
+            return rho[:k], u[:3 * k].view(3, k), phi[:k]
+        rho, u, phi = np.empty(max(k, 1)), np.empty(3 * max(k, 1)), np.empty(max(k, 1))
+        L.check(L.lib().lb_moments_masked(self.handle, mp, rho.ctypes.data, u.ctypes.data, phi.ctypes.data,
+                                          ctypes.byref(cnt), kind), "lb_moments_masked")
+        return rho[:k], u[:3 * k].reshape(3, k), phi[:k]
+
+    def get_state_masked(self, mask):
+        """(f [19,k], g [19,k]) post-streaming distributions of the k selected
+        sites in site order."""
+        mp, kind, keep = self._mask(mask)
+        k = self.count_masked(mask)
+        cnt = ctypes.c_longlong(0)
+        if kind == L.LB_DEVICE:
+            torch = _torch()
+            f = torch.empty(19 * max(k, 1), dtype=torch.float64, device="cuda")
+            g = torch.empty_like(f)
+            L.check(L.lib().lb_get_state_masked(self.handle, mp, f.data_ptr(), g.data_ptr(), ctypes.byref(cnt),
+                                                kind), "lb_get_state_masked")
+            return f[:19 * k].view(19, k), g[:19 * k].view(19, k)
+        f, g = np.empty(19 * max(k, 1)), np.empty(19 * max(k, 1))
+        L.check(L.lib().lb_get_state_masked(self.handle, mp, f.ctypes.data, g.ctypes.data, ctypes.byref(cnt),
+                                            kind), "lb_get_state_masked")
+        return f[:19 * k].reshape(19, k), g[:19 * k].reshape(19, k)
+
+    def set_state_masked(self, mask, f, g):
+        """Overwrite the post-streaming f, g ([19,k] each) of the k selected
+        sites."""
+        mp, kind, keep = self._mask(mask)
+        k = self.count_masked(mask)
+        fp, fk, k1 = _ptr_of(f, 19 * k, "f")
+        gp, gk, k2 = _ptr_of(g, 19 * k, "g")
+        if fk != kind or gk != kind:
+            raise ValueError("mask, f and g must all be host or all be device arrays")
+        L.check(L.lib().lb_set_state_masked(self.handle, mp, fp, gp, kind), "lb_set_state_masked")
+
 
 # ABI velocity order (include/lb.h)
 VELOCITIES = np.array([
