@@ -16,6 +16,7 @@ Under torchrun (N > 1) every rank advances its own replica of the lattice
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -42,6 +43,7 @@ ORACLE_SAMPLE = (64, 64, 64)
 ORACLE_STEPS = 30
 E2E_STEPS = 50
 MRT_RATES = (1.3, 0.6)      # tau_bulk, tau_ghost of the MRT measurement
+MASK_DENSITY = 0.1          # fraction of sites selected in the masked-moments measurement
 FALLBACK_HBM = 6800.0
 # kernels one timestep launches, per lb_set_kernel choice
 STEP_KERNELS = {"auto": "timestep = k_phi_pull + k_collide_pull (two launches)",
@@ -331,6 +333,40 @@ def run_ours(args):
 
     # the tau_g = 1 reduced form on the same workload (the workload has tau_g = 1)
     reduced = {prec: timed(prec, "taug1", 7) for prec in ("fp32_shifted", "fp64")}
+    # masked moments (stream compaction) of a seeded 10 % site mask on the
+    # benchmark lattice after the warm-up steps
+    with Lattice.from_params(DIMS, params, precision="fp32_shifted") as lat:
+        lat.init(phi0)
+        lat.step(args.warmup)
+        mask = torch.from_numpy((LI.uniform(77, n, 0.0, 1.0) < MASK_DENSITY).astype(np.uint8)).cuda()
+        k_sel = lat.count_masked(mask)
+        outs = [torch.empty(m * k_sel, dtype=torch.float64, device="cuda") for m in (1, 3, 1)]
+        from paper_1405_6162_gb300 import _lib as LL
+        lib = LL.lib()
+        cnt = ctypes.c_longlong(0)
+
+        def masked_call():
+            rc = lib.lb_moments_masked(lat.handle, mask.data_ptr(), outs[0].data_ptr(), outs[1].data_ptr(),
+                                       outs[2].data_ptr(), ctypes.byref(cnt), LL.LB_DEVICE)
+            assert rc == 0
+        for _ in range(3):
+            masked_call()
+        barrier()
+        reps = 20
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(reps):
+            masked_call()
+        ev1.record()
+        ev1.synchronize()
+        t_mask = ev0.elapsed_time(ev1) / 1e3 / reps
+    masked = {"density": MASK_DENSITY, "selected": k_sel, "ms_per_call": t_mask * 1e3,
+              "selected_sites_per_s": k_sel / t_mask,
+              # mask read twice (count, gather) + per selected site: 19 f + 19 g pulled (float) + 5 doubles out
+              "algorithmic_bytes": 2 * n + k_sel * (38 * 4 + 5 * 8)}
+    masked["achieved_gbs"] = masked["algorithmic_bytes"] / t_mask / 1e9
+    masked["hbm_frac"] = masked["achieved_gbs"] / peak
+
     # the MRT collision of f on the default step
     mrt = {prec: timed(prec, "auto", 7, MRT_RATES) for prec in ("fp32_shifted", "fp64")}
     # the isotropic stencils on the default step
@@ -347,7 +383,8 @@ def run_ours(args):
         lat.init(phi_host)
         lat.step(2)
         lbl = lat.handle
-        lib = __import__("paper_1405_6162_gb300._lib", fromlist=["lib"]).lib()
+        from paper_1405_6162_gb300 import _lib as LL
+        lib = LL.lib()
         barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_iters):
@@ -461,6 +498,10 @@ def run_ours(args):
         "mrt": {"what": f"multiple-relaxation-time collision of f (lb_set_collision), tau = 1, "
                         f"tau_bulk = {MRT_RATES[0]}, tau_ghost = {MRT_RATES[1]}, on the default two-pass step",
                 "fp32_shifted": mrt_for("fp32_shifted"), "fp64": mrt_for("fp64")},
+        "masked_moments": {"what": "lb_moments_masked (stream compaction: count, scan, gather) of a seeded "
+                                   "random site mask on the 256^3 FP32 lattice, device outputs, one call "
+                                   "includes the read-back of the count",
+                           **masked},
         "stencils": {"what": "isotropic 19- / 27-point phi stencils (lb_set_stencil) on the default "
                              "two-pass step; hbm_frac over the same 76-word algorithmic bytes",
                      **{f"{npts}pt": {prec: stencil_for(npts, prec) for prec in ("fp32_shifted", "fp64")}
@@ -528,6 +569,12 @@ def run_step_only(args):
         lat.step(args.steps)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        if args.masked is not None:
+            n = math.prod(dims)
+            mask = torch.from_numpy((LI.uniform(77, n, 0.0, 1.0) < args.masked).astype(np.uint8)).cuda()
+            for _ in range(3):
+                lat.moments_masked(mask)
+            torch.cuda.synchronize()
     print(json.dumps({"only": "step", "lattice": list(dims), "precision": args.precision, "launch": list(cfg),
                       "stencil": args.stencil,
                       "steps": args.steps, "MLUPS": math.prod(dims) * args.steps / dt / 1e6}))
@@ -550,6 +597,8 @@ def main():
                     help="points of the phi stencil of the --only lattice")
     ap.add_argument("--mrt", type=float, nargs=2, default=None, metavar=("TAU_BULK", "TAU_GHOST"),
                     help="MRT collision of the --only lattice")
+    ap.add_argument("--masked", type=float, default=None, metavar="DENSITY",
+                    help="after the steps, three masked-moment copies of a random mask of this density")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

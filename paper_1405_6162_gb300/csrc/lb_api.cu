@@ -536,19 +536,19 @@ int lb_moments_masked(lb_ctx *c, const unsigned char *mask, double *rho, double 
     if (rc) return rc;
     if (count) *count = total;
     if (total == 0 || (!rho && !u && !phi)) return LB_OK;
-    if (ptr_kind == LB_DEVICE) return lbk::launch_masked_moments(c, mask_d, c->mask_scratch, rho, u, phi);
+    if (ptr_kind == LB_DEVICE) return lbk::launch_masked_moments(c, total, c->mask_scratch, rho, u, phi);
     rc = ensure_io(c);
     if (rc) return rc;
     const size_t nb = (size_t)total * sizeof(double);
     // rho and u through the staging buffer (4 total values), then phi
     if (rho || u) {
-        rc = lbk::launch_masked_moments(c, mask_d, c->mask_scratch, c->io, c->io + total, nullptr);
+        rc = lbk::launch_masked_moments(c, total, c->mask_scratch, c->io, c->io + total, nullptr);
         if (!rc && rho) rc = copy(c, rho, c->io, nb, cudaMemcpyDeviceToHost);
         if (!rc && u) rc = copy(c, u, c->io + total, 3 * nb, cudaMemcpyDeviceToHost);
         if (!rc) rc = sync(c);
     }
     if (!rc && phi) {
-        rc = lbk::launch_masked_moments(c, mask_d, c->mask_scratch, nullptr, nullptr, c->io);
+        rc = lbk::launch_masked_moments(c, total, c->mask_scratch, nullptr, nullptr, c->io);
         if (!rc) rc = copy(c, phi, c->io, nb, cudaMemcpyDeviceToHost);
         if (!rc) rc = sync(c);
     }
@@ -571,7 +571,7 @@ static int masked_state(lb_ctx *c, const unsigned char *mask, double *f, double 
     if (ptr_kind == LB_DEVICE) {
         for (int which = 0; which < 2 && !rc; which++) {
             double *buf = to_device_state ? const_cast<double *>(in[which]) : out[which];
-            if (buf) rc = lbk::launch_masked_rows(c, mask_d, c->mask_scratch, which, 0, lbk::Q, buf, to_device_state);
+            if (buf) rc = lbk::launch_masked_rows(c, total, c->mask_scratch, which, 0, lbk::Q, buf, to_device_state);
         }
         return rc;
     }
@@ -585,9 +585,9 @@ static int masked_state(lb_ctx *c, const unsigned char *mask, double *f, double 
             const size_t bytes = (size_t)(i1 - i0) * T * sizeof(double);
             if (to_device_state) {
                 rc = copy(c, c->io, in[which] + (size_t)i0 * T, bytes, cudaMemcpyHostToDevice);
-                if (!rc) rc = lbk::launch_masked_rows(c, mask_d, c->mask_scratch, which, i0, i1, c->io, 1);
+                if (!rc) rc = lbk::launch_masked_rows(c, total, c->mask_scratch, which, i0, i1, c->io, 1);
             } else {
-                rc = lbk::launch_masked_rows(c, mask_d, c->mask_scratch, which, i0, i1, c->io, 0);
+                rc = lbk::launch_masked_rows(c, total, c->mask_scratch, which, i0, i1, c->io, 0);
                 if (!rc) rc = copy(c, out[which] + (size_t)i0 * T, c->io, bytes, cudaMemcpyDeviceToHost);
             }
             if (!rc) rc = sync(c);

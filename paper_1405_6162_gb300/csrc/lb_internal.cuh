@@ -171,10 +171,9 @@ int taug1_phi_out(lb_ctx *c, double *out);
 size_t masked_scratch_ints(long long N);
 int masked_total_offset(long long N);
 int launch_mask_scan(lb_ctx *c, const unsigned char *mask_d, int *scratch);
-int launch_masked_moments(lb_ctx *c, const unsigned char *mask_d, const int *scratch, double *rho, double *u,
-                          double *phi);
-int launch_masked_rows(lb_ctx *c, const unsigned char *mask_d, const int *scratch, int which, int i0, int i1,
-                       double *io, int to_device_state);
+int launch_masked_moments(lb_ctx *c, long long total, const int *scratch, double *rho, double *u, double *phi);
+int launch_masked_rows(lb_ctx *c, long long total, const int *scratch, int which, int i0, int i1, double *io,
+                       int to_device_state);
 
 // lagged kernel (lb_lag.cu)
 int launch_step_lag(lb_ctx *c, int nsteps);

@@ -2,12 +2,13 @@
 // sites whose mask byte is non-zero, in site order (targetDP Sec. III.B,
 // copyFromTargetMasked / copyToTargetMasked).
 //
-// A stream compaction in three launches: per-CTA counts of selected sites
-// (one site per thread, __syncthreads_count), one CTA's exclusive scan of the
-// counts (offsets[nb] = total), then the gather or scatter kernel, whose
-// threads find their compact index from the CTA offset, the warp prefix of
-// the warps before them and a ballot within their warp.  The order is the
-// site order, so the result is unique and bit-exact.
+// A stream compaction: per-CTA counts of selected sites (one site per thread,
+// __syncthreads_count), one CTA's exclusive scan of the counts (offsets[nb] =
+// total), then the list of selected sites, each thread placing its site by
+// the CTA offset, the warp prefix of the warps before it and a ballot within
+// its warp.  The gather / scatter kernels then run one thread per selected
+// site, so every thread has work whatever the mask's density.  The order is
+// the site order, so the result is unique and bit-exact.
 #include <cuda_runtime.h>
 
 #include "d3q19.cuh"
@@ -91,41 +92,50 @@ __device__ __forceinline__ int compact_index(bool flag, const int *__restrict__ 
     return offsets[blockIdx.x] + warp_pre[warp] + before;
 }
 
-// rho, u = (sum f c + F/2)/rho, phi of the selected sites; u as [3][total].
-// REDUCED: phi is component 0 of the g level (the tau_g = 1 form).
-template <typename T, bool SH, bool REDUCED>
-__global__ void __launch_bounds__(kMaskThreads) k_masked_moments(
-    const T *__restrict__ fa, const T *__restrict__ ga, const unsigned char *__restrict__ mask,
-    const int *__restrict__ offsets, int nb, double rho0, double hFx, double hFy, double hFz,
-    double *__restrict__ rho, double *__restrict__ u, double *__restrict__ phi, int nx, int ny, int nz, long long S)
+// idx[k] = site of the k-th selected site (site order)
+__global__ void __launch_bounds__(kMaskThreads) k_mask_index(const unsigned char *__restrict__ mask, long long N,
+                                                             const int *__restrict__ offsets, int *__restrict__ idx)
 {
-    const long long N = (long long)nx * ny * nz;
     const long long s = (long long)blockIdx.x * kMaskThreads + threadIdx.x;
     const bool flag = s < N && mask[s] != 0;
     const int dst = compact_index(flag, offsets);
-    if (!flag) return;
-    const long long total = offsets[nb];
-    const Nbr n((int)s, nx, ny, nz);
+    if (flag) idx[dst] = (int)s;
+}
+
+constexpr int kGatherThreads = 256;   // one selected site per thread
+
+// rho, u = (sum f c + F/2)/rho, phi of the selected sites; u as [3][total].
+// REDUCED: phi is component 0 of the g level (the tau_g = 1 form).
+template <typename T, bool SH, bool REDUCED>
+__global__ void __launch_bounds__(kGatherThreads) k_masked_moments(
+    const T *__restrict__ fa, const T *__restrict__ ga, const int *__restrict__ idx, int total, double rho0,
+    double hFx, double hFy, double hFz, double *__restrict__ rho, double *__restrict__ u, double *__restrict__ phi,
+    int nx, int ny, int nz, long long S)
+{
+    const int k = blockIdx.x * kGatherThreads + threadIdx.x;
+    if (k >= total) return;
+    const int s = idx[k];
+    const Nbr n(s, nx, ny, nz);
     double f[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) f[i] = double(fa[(size_t)i * S + n.src(i)]);
     double R, jx, jy, jz;
     density_moments(f, R, jx, jy, jz);
     const double r = SH ? rho0 + R : R;
-    if (rho) rho[dst] = r;
+    if (rho) rho[k] = r;
     if (u) {
-        u[dst] = (jx + hFx) / r;
-        u[total + dst] = (jy + hFy) / r;
-        u[2 * total + dst] = (jz + hFz) / r;
+        u[k] = (jx + hFx) / r;
+        u[(size_t)total + k] = (jy + hFy) / r;
+        u[2 * (size_t)total + k] = (jz + hFz) / r;
     }
     if (phi) {
         if (REDUCED) {
-            phi[dst] = double(ga[s]);
+            phi[k] = double(ga[s]);
         } else {
             double g[Q];
 #pragma unroll
             for (int i = 0; i < Q; i++) g[i] = double(ga[(size_t)i * S + n.src(i)]);
-            phi[dst] = sum19(g);
+            phi[k] = sum19(g);
         }
     }
 }
@@ -133,78 +143,73 @@ __global__ void __launch_bounds__(kMaskThreads) k_masked_moments(
 // rows [i0, i1) of the post-streaming state A_i(x - c_i) + w_i shift at the
 // selected sites, out[(i - i0) * total + k]
 template <typename T>
-__global__ void __launch_bounds__(kMaskThreads) k_masked_get(const T *__restrict__ a,
-                                                             const unsigned char *__restrict__ mask,
-                                                             const int *__restrict__ offsets, int nb, int i0, int i1,
-                                                             double shift, double *__restrict__ out, int nx, int ny,
-                                                             int nz, long long S)
+__global__ void __launch_bounds__(kGatherThreads) k_masked_get(const T *__restrict__ a, const int *__restrict__ idx,
+                                                               int total, int i0, int i1, double shift,
+                                                               double *__restrict__ out, int nx, int ny, int nz,
+                                                               long long S)
 {
-    const long long N = (long long)nx * ny * nz;
-    const long long s = (long long)blockIdx.x * kMaskThreads + threadIdx.x;
-    const bool flag = s < N && mask[s] != 0;
-    const int dst = compact_index(flag, offsets);
-    if (!flag) return;
-    const long long total = offsets[nb];
-    const Nbr n((int)s, nx, ny, nz);
+    const int k = blockIdx.x * kGatherThreads + threadIdx.x;
+    if (k >= total) return;
+    const Nbr n(idx[k], nx, ny, nz);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         if (i < i0 || i >= i1) continue;
-        out[(size_t)(i - i0) * total + dst] = double(a[(size_t)i * S + n.src(i)]) + weight(i) * shift;
+        out[(size_t)(i - i0) * total + k] = double(a[(size_t)i * S + n.src(i)]) + weight(i) * shift;
     }
 }
 
 // the inverse: A_i(x - c_i) = in[(i - i0) * total + k] - w_i shift at the
 // selected sites
 template <typename T>
-__global__ void __launch_bounds__(kMaskThreads) k_masked_set(T *__restrict__ a, const unsigned char *__restrict__ mask,
-                                                             const int *__restrict__ offsets, int nb, int i0, int i1,
-                                                             double shift, const double *__restrict__ in, int nx,
-                                                             int ny, int nz, long long S)
+__global__ void __launch_bounds__(kGatherThreads) k_masked_set(T *__restrict__ a, const int *__restrict__ idx,
+                                                               int total, int i0, int i1, double shift,
+                                                               const double *__restrict__ in, int nx, int ny, int nz,
+                                                               long long S)
 {
-    const long long N = (long long)nx * ny * nz;
-    const long long s = (long long)blockIdx.x * kMaskThreads + threadIdx.x;
-    const bool flag = s < N && mask[s] != 0;
-    const int dst = compact_index(flag, offsets);
-    if (!flag) return;
-    const long long total = offsets[nb];
-    const Nbr n((int)s, nx, ny, nz);
+    const int k = blockIdx.x * kGatherThreads + threadIdx.x;
+    if (k >= total) return;
+    const Nbr n(idx[k], nx, ny, nz);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         if (i < i0 || i >= i1) continue;
-        a[(size_t)i * S + n.src(i)] = T(in[(size_t)(i - i0) * total + dst] - weight(i) * shift);
+        a[(size_t)i * S + n.src(i)] = T(in[(size_t)(i - i0) * total + k] - weight(i) * shift);
     }
 }
 
 inline int mask_blocks(long long N) { return (int)((N + kMaskThreads - 1) / kMaskThreads); }
 
+inline unsigned gather_blocks(long long total) { return (unsigned)((total + kGatherThreads - 1) / kGatherThreads); }
+
 }  // namespace
 
-size_t masked_scratch_ints(long long N) { return 2 * (size_t)mask_blocks(N) + 1; }
+// scratch: counts [nb], offsets [nb + 1], site indices [N]
+size_t masked_scratch_ints(long long N) { return 2 * (size_t)mask_blocks(N) + 1 + (size_t)N; }
 
-// counts and offsets of the selected sites (scratch: masked_scratch_ints ints)
+// counts, offsets and site indices of the selected sites
 int launch_mask_scan(lb_ctx *c, const unsigned char *mask_d, int *scratch)
 {
     const int nb = mask_blocks(c->N);
-    int *counts = scratch, *offsets = scratch + nb;
+    int *counts = scratch, *offsets = scratch + nb, *idx = scratch + 2 * nb + 1;
     k_mask_count<<<nb, kMaskThreads, 0, c->stream>>>(mask_d, c->N, counts);
     k_mask_scan<<<1, kMaskThreads, 0, c->stream>>>(counts, nb, offsets);
+    k_mask_index<<<nb, kMaskThreads, 0, c->stream>>>(mask_d, c->N, offsets, idx);
     return check_launch();
 }
 
 int masked_total_offset(long long N) { return 2 * mask_blocks(N); }   // index of offsets[nb] in the scratch
 
-int launch_masked_moments(lb_ctx *c, const unsigned char *mask_d, const int *scratch, double *rho, double *u,
-                          double *phi)
+int launch_masked_moments(lb_ctx *c, long long total, const int *scratch, double *rho, double *u, double *phi)
 {
-    const int nb = mask_blocks(c->N);
-    const int *offsets = scratch + nb;
+    if (total <= 0) return LB_OK;
+    const int *idx = scratch + 2 * mask_blocks(c->N) + 1;
     const int cur = c->buf.cur;
     const double hF[3] = {0.5 * c->force[0], 0.5 * c->force[1], 0.5 * c->force[2]};
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
-#define LBK_MM(T, SH, RED)                                                                                      \
-    k_masked_moments<T, SH, RED><<<nb, kMaskThreads, 0, c->stream>>>(                                          \
-        (const T *)c->buf.f[cur], (const T *)c->buf.g[cur], mask_d, offsets, nb, c->p.rho0, hF[0], hF[1], hF[2], \
-        rho, u, phi, nx, ny, nz, c->S)
+    const unsigned grid = gather_blocks(total);
+#define LBK_MM(T, SH, RED)                                                                                        \
+    k_masked_moments<T, SH, RED><<<grid, kGatherThreads, 0, c->stream>>>(                                        \
+        (const T *)c->buf.f[cur], (const T *)c->buf.g[cur], idx, (int)total, c->p.rho0, hF[0], hF[1], hF[2], rho, \
+        u, phi, nx, ny, nz, c->S)
     if (c->p.precision == LB_FP64) {
         if (c->reduced)
             LBK_MM(double, false, true);
@@ -220,29 +225,31 @@ int launch_masked_moments(lb_ctx *c, const unsigned char *mask_d, const int *scr
     return check_launch();
 }
 
-int launch_masked_rows(lb_ctx *c, const unsigned char *mask_d, const int *scratch, int which, int i0, int i1,
-                       double *io, int to_device_state)
+int launch_masked_rows(lb_ctx *c, long long total, const int *scratch, int which, int i0, int i1, double *io,
+                       int to_device_state)
 {
-    const int nb = mask_blocks(c->N);
-    const int *offsets = scratch + nb;
+    if (total <= 0) return LB_OK;
+    const int *idx = scratch + 2 * mask_blocks(c->N) + 1;
     const int cur = c->buf.cur;
     const double shift = (which == 0 && c->p.precision == LB_FP32_SHIFTED) ? c->p.rho0 : 0.0;
     void *a = which == 0 ? c->buf.f[cur] : c->buf.g[cur];
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    const unsigned grid = gather_blocks(total);
+    const int tot = (int)total;
     if (c->p.precision == LB_FP64) {
         if (to_device_state)
-            k_masked_set<double><<<nb, kMaskThreads, 0, c->stream>>>((double *)a, mask_d, offsets, nb, i0, i1, shift,
-                                                                     io, nx, ny, nz, c->S);
+            k_masked_set<double><<<grid, kGatherThreads, 0, c->stream>>>((double *)a, idx, tot, i0, i1, shift, io,
+                                                                         nx, ny, nz, c->S);
         else
-            k_masked_get<double><<<nb, kMaskThreads, 0, c->stream>>>((const double *)a, mask_d, offsets, nb, i0, i1,
-                                                                     shift, io, nx, ny, nz, c->S);
+            k_masked_get<double><<<grid, kGatherThreads, 0, c->stream>>>((const double *)a, idx, tot, i0, i1, shift,
+                                                                         io, nx, ny, nz, c->S);
     } else {
         if (to_device_state)
-            k_masked_set<float><<<nb, kMaskThreads, 0, c->stream>>>((float *)a, mask_d, offsets, nb, i0, i1, shift, io,
-                                                                    nx, ny, nz, c->S);
+            k_masked_set<float><<<grid, kGatherThreads, 0, c->stream>>>((float *)a, idx, tot, i0, i1, shift, io, nx,
+                                                                        ny, nz, c->S);
         else
-            k_masked_get<float><<<nb, kMaskThreads, 0, c->stream>>>((const float *)a, mask_d, offsets, nb, i0, i1,
-                                                                    shift, io, nx, ny, nz, c->S);
+            k_masked_get<float><<<grid, kGatherThreads, 0, c->stream>>>((const float *)a, idx, tot, i0, i1, shift,
+                                                                        io, nx, ny, nz, c->S);
     }
     return check_launch();
 }
