@@ -7,6 +7,7 @@
 
 #include "d3q19.cuh"
 #include "lb.h"
+#include "lb_coll.cuh"
 
 #ifndef LBK_COMPONENT_PAD
 #define LBK_COMPONENT_PAD 0
@@ -69,60 +70,17 @@ inline bool uses_mrt(const lb_ctx *c)
     return c->collision == LB_COLLISION_MRT || c->force[0] != 0.0 || c->force[1] != 0.0 || c->force[2] != 0.0;
 }
 
-// MRT rates and force in the arithmetic type T; BGK with a force uses the
-// shear rate for all three rates (Guo's BGK scheme)
+// MRT rates and force of the context in the arithmetic type T
 template <typename T>
 inline Mrt<T> make_mrt(const lb_ctx *c)
 {
-    const double ws = 1.0 / c->p.tau;
-    const bool mrt = c->collision == LB_COLLISION_MRT;
-    const double wb = mrt ? 1.0 / c->tau_bulk : ws, wg = mrt ? 1.0 / c->tau_ghost : ws;
-    Mrt<T> m;
-    m.cs = T(1.0 - ws);
-    m.cb = T(1.0 - wb);
-    m.hs = T(1.0 - 0.5 * ws);
-    m.hb = T(1.0 - 0.5 * wb);
-    m.og = T(wg);
-    m.cgh = T(1.0 - wg);
-    m.kf = T(1.0 - 0.5 * wg);
-    m.Fx = T(c->force[0]);
-    m.Fy = T(c->force[1]);
-    m.Fz = T(c->force[2]);
-    m.hFx = T(0.5 * c->force[0]);
-    m.hFy = T(0.5 * c->force[1]);
-    m.hFz = T(0.5 * c->force[2]);
-    return m;
+    return make_mrt<T>(c->p, c->collision == LB_COLLISION_MRT, c->tau_bulk, c->tau_ghost, c->force);
 }
 
 constexpr int kLagBlock = 256;       // sites per block of the lagged kernel
 constexpr long long kLagSlack = 128;  // extra lag (blocks) beyond the stencil reach
 constexpr int kReduceBlocks = 608;   // 4 x 152 SMs; fixed so sums are reproducible
 constexpr int kReduceThreads = 256;
-
-// Parameters of the step in the arithmetic type T (constants formed in
-// double, rounded once).
-template <typename T>
-inline Coll<T> make_coll(const lb_params &p)
-{
-    const double om = 1.0 / p.tau, og = 1.0 / p.tau_g;
-    Coll<T> c;
-    c.omega = T(om);
-    c.omega_g = T(og);
-    c.rho0 = T(p.rho0);
-    c.gamma = T(p.gamma);
-    c.A = T(p.A);
-    c.B = T(p.B);
-    c.kappa = T(p.kappa);
-    c.cf = T(1.0 - om);
-    c.f0 = T(om / 3.0);  c.f1 = T(om / 18.0);  c.f2 = T(om / 36.0);
-    c.f1h = T(om / 4.0); c.f2h = T(om / 8.0);
-    c.f1t = T(om / 6.0); c.f2t = T(om / 12.0);
-    c.cg = T(1.0 - og);
-    c.g0 = T(og / 3.0);  c.g1 = T(og / 18.0);  c.g2 = T(og / 36.0);
-    c.g1h = T(og / 4.0); c.g2h = T(og / 8.0);
-    c.g1t = T(og / 6.0); c.g2t = T(og / 12.0);
-    return c;
-}
 
 // ensemble membership (lb_api.cu): the member shares the batch's error flag
 void adopt_into_batch(lb_ctx *c, unsigned int *shared_err);
