@@ -247,6 +247,22 @@ __device__ __forceinline__ void collide_g(const Coll<T>& p, T (&g)[Q], T phi, T 
     LBK_GEDGE(15, 16, py + pz, uy + uz)
     LBK_GEDGE(17, 18, py - pz, uy - uz)
 #undef LBK_GEDGE
+    if constexpr (sizeof(T) == 4) {
+        // In float the folded weights do not sum to omega_g (1/3 + 6/18 +
+        // 12/36 rounds to 1 + 1.5e-8), which would bias sum g* -- phi -- by
+        // that fraction every step.  The rest value takes up the difference
+        // instead: g*_0 = phi - sum_{i>0} g*_i, the sum with its rounding
+        // errors carried (TwoSum), so phi is conserved up to unbiased rounding.
+        T s = g[1], c = T(0);
+#pragma unroll
+        for (int i = 2; i < Q; i++) {
+            const T t = s + g[i];
+            const T bp = t - s;
+            c += (s - (t - bp)) + (g[i] - bp);
+            s = t;
+        }
+        g[0] = (phi - s) - c;
+    }
 }
 
 // In-place BGK collision of f (collide_f) and of g at one site.

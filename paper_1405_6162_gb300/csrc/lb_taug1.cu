@@ -88,7 +88,19 @@ template <typename T>
 __device__ __forceinline__ T geq_eq(int i, const Eq<T> &e)
 {
     const int c2 = cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i);
-    if (c2 == 0) return T(weight(0)) * e.b0;
+    if (c2 == 0) {
+        if constexpr (sizeof(T) == 4) {
+            // the float weights sum to 1 + e1 and their (c^2 - 1) moment is e2
+            // instead of 0 (e1, e2 from the rounded values); the rest term
+            // removes the bias e1 P + e2 gmh they would give sum_i geq_i
+            constexpr double w0f = double(float(1.0 / 3.0)), w1f = double(float(1.0 / 18.0)),
+                             w2f = double(float(1.0 / 36.0));
+            constexpr float e1 = float(w0f + 6.0 * w1f + 12.0 * w2f - 1.0);
+            constexpr float e2 = float(12.0 * w2f - w0f);
+            return T(weight(0)) * e.b0 - (e1 * e.b1 + e2 * (e.b1 - e.b0));
+        }
+        return T(weight(0)) * e.b0;
+    }
     const T cu = cdot(i, e.ux, e.uy, e.uz);
     const T base = c2 == 1 ? e.b1 : e.b2;
     return T(weight(i)) * (base + cu * (e.a3 + e.a45 * cu));

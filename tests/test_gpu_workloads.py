@@ -38,21 +38,32 @@ def spinodal_reference():
     return dims, phi0, oracle.moments(dims, f, g), u_scale(f)
 
 
-@pytest.mark.parametrize("precision,bounds", [
-    ("fp64", {"rho": 1e-11, "u": 1e-11, "phi": 1e-11}),
-    ("fp32_shifted", {"rho": 1e-6, "u": 1e-6, "phi": 1e-4}),
+@pytest.mark.parametrize("precision,kernel,bounds", [
+    ("fp64", "auto", {"rho": 1e-11, "u": 1e-11, "phi": 1e-11}),
+    ("fp32_shifted", "auto", {"rho": 1e-7, "u": 1e-7, "phi": 1e-5}),
+    ("fp64", "taug1", {"rho": 1e-11, "u": 1e-11, "phi": 1e-11}),
+    ("fp32_shifted", "taug1", {"rho": 1e-7, "u": 1e-7, "phi": 1e-5}),
 ])
-def test_spinodal_64cubed_1000_steps(spinodal_reference, precision, bounds):
+def test_spinodal_64cubed_1000_steps(spinodal_reference, precision, kernel, bounds):
+    """The FP32 bounds are the 1e-5 aimed for (measured: phi 3.0e-6 two-pass,
+    6.5e-6 reduced form; rho, u ~3e-8)."""
     from paper_1405_6162_gb300 import Lattice
     dims, phi0, want, us = spinodal_reference
     with Lattice.from_params(dims, P0, precision=precision) as lat:
+        lat.set_kernel(kernel)
         lat.init(phi0)
+        r0 = lat.reduce()
         lat.step(1000)
+        r1 = lat.reduce()
         got = lat.moments()
     errs = {k: rel(a, b, us if k == "u" else None) for k, a, b in zip(("rho", "u", "phi"), got, want)}
-    print(f"spinodal 64^3 x 1000 {precision}: {errs}  (max|phi| = {np.abs(want[2]).max():.3f})")
+    print(f"spinodal 64^3 x 1000 {precision} {kernel}: {errs}  (max|phi| = {np.abs(want[2]).max():.3f})")
     for k, e in errs.items():
         assert e <= bounds[k], (k, e)
+    # sum phi is conserved up to unbiased rounding (float weights that do not
+    # sum to 1 would drift it by ~1.5e-8 of sum |phi| per step, 1.5e-5 here)
+    drift = abs(r1[4] - r0[4]) / np.abs(got[2]).sum()
+    assert drift < (1e-13 if precision == "fp64" else 1e-6), drift
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_shifted"])
