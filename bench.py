@@ -178,7 +178,7 @@ def _oracle_errors(torch, params):
     c, _ = oracle.velocity_set()
     us = float(((np.abs(f).T @ np.abs(c).astype(float)) / f.sum(0)[:, None]).max())
     errs = {}
-    for prec in ("fp64", "fp32_shifted"):
+    for prec in ("fp64", "fp32_shifted", "fp64_df"):
         with Lattice.from_params(dims, params, precision=prec) as lat:
             lat.init(phi0)
             lat.step(ORACLE_STEPS)
@@ -367,6 +367,9 @@ def run_ours(args):
     masked["achieved_gbs"] = masked["algorithmic_bytes"] / t_mask / 1e9
     masked["hbm_frac"] = masked["achieved_gbs"] / peak
 
+    # double-float (FP64-class accuracy on the FP32 units) on the default step
+    df = timed("fp64_df", "auto", 7)
+
     # the MRT collision of f on the default step
     mrt = {prec: timed(prec, "auto", 7, MRT_RATES) for prec in ("fp32_shifted", "fp64")}
     # the isotropic stencils on the default step
@@ -470,6 +473,18 @@ def run_ours(args):
                               "frac": fl * n / r["t_launch"] / 1e12 / pk, "flops_per_site": fl}
         return out
 
+    def df_line():
+        r = df
+        achieved = BYTES_PER_SITE["fp64"] * n / r["t_launch"] / 1e9
+        return {"value": ws * n * r["steps"] / r["wall"] / 1e6, "unit": "MLUPS", "steps": r["steps"],
+                "ms_per_step": r["wall"] / r["steps"] * 1e3, "clocks": r["clocks"],
+                "speedup_vs_fp64": (r["steps"] / r["wall"]) / (args.steps / results["fp64"]["wall"]),
+                "roofline": {"bound": "alu (FP32 pipe) / hbm", "kernel": STEP_KERNELS["two_pass"],
+                             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                             "traffic": _profile_value("step_fp64_df_256cubed", "dram_bytes_per_step"),
+                             "peak_kind": f"{peak_kind} (copy bandwidth)",
+                             "algorithmic_bytes_per_launch": BYTES_PER_SITE["fp64"] * n}}
+
     v32, roof32 = line_for("fp32_shifted")
     v64, roof64 = line_for("fp64")
     r32 = results["fp32_shifted"]
@@ -495,6 +510,9 @@ def run_ours(args):
         "taug1": {"what": "tau_g = 1 reduced form (LB_KERNEL_TAUG1): g kept as phi and (gmh, u), "
                           "same results as the general step to rounding; valid only at tau_g = 1",
                   "fp32_shifted": reduced_for("fp32_shifted"), "fp64": reduced_for("fp64")},
+        "fp64_df": {"what": "double-float precision (LB_FP64_DF): every value an unevaluated sum of two floats "
+                            "(~48 bits), arithmetic on the FP32 units; errors in error_vs_oracle.fp64_df",
+                    **df_line()},
         "mrt": {"what": f"multiple-relaxation-time collision of f (lb_set_collision), tau = 1, "
                         f"tau_bulk = {MRT_RATES[0]}, tau_ghost = {MRT_RATES[1]}, on the default two-pass step",
                 "fp32_shifted": mrt_for("fp32_shifted"), "fp64": mrt_for("fp64")},
@@ -589,7 +607,7 @@ def main():
     ap.add_argument("--only", choices=["step"], default=None,
                     help="run only timesteps of one lattice (profiling case)")
     ap.add_argument("--lattice", type=int, default=128, help="edge of the --only lattice")
-    ap.add_argument("--precision", choices=["fp32_shifted", "fp64"], default="fp32_shifted")
+    ap.add_argument("--precision", choices=["fp32_shifted", "fp64", "fp64_df"], default="fp32_shifted")
     ap.add_argument("--kernel", choices=["two_pass", "fused", "staged", "slab", "lag", "taug1"], default=None,
                     help="override the tuned launch of the --only lattice")
     ap.add_argument("--block", type=int, nargs=3, default=(0, 0, 0), metavar=("BX", "BY", "ZC"))

@@ -64,8 +64,14 @@ enum {
 /* Storage/arithmetic precision of the distributions. */
 enum {
     LB_FP64 = 0,          /* f, g stored and computed in double               */
-    LB_FP32_SHIFTED = 1   /* float storage and arithmetic of f_i - w_i rho0
+    LB_FP32_SHIFTED = 1,  /* float storage and arithmetic of f_i - w_i rho0
                              and of g_i; FP64 only in lb_reduce's sums         */
+    LB_FP64_DF = 2        /* double-float: each value stored and computed as
+                             an unevaluated sum of two floats (~48 bits,
+                             unit roundoff ~2^-48), on the FP32 units; the
+                             default two-pass step only (LB_KERNEL_AUTO /
+                             LB_KERNEL_TWO_PASS), not in ensembles or the
+                             adjoint                                         */
 };
 
 enum { LB_HOST = 0, LB_DEVICE = 1 };

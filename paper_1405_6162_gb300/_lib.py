@@ -22,6 +22,7 @@ LB_ERR_TIMEOUT = -5
 
 LB_FP64 = 0
 LB_FP32_SHIFTED = 1
+LB_FP64_DF = 2
 LB_HOST = 0
 LB_DEVICE = 1
 LB_COLLISION_BGK = 0

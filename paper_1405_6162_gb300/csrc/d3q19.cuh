@@ -19,6 +19,15 @@ namespace lbk {
 
 constexpr int Q = 19;
 
+
+// a * b + c; one fused operation for float and double (contracted), and the
+// fused double-float form for df64 (df64.cuh)
+template <typename T>
+__device__ __forceinline__ T fmadd(T a, T b, T c)
+{
+    return a * b + c;
+}
+
 template <typename T>
 __device__ __forceinline__ void store(T *p, T v)
 {
@@ -180,13 +189,13 @@ __device__ __forceinline__ void collide_f(const Coll<T>& p, T (&f)[Q], T phi, T 
     // ---- f: omega feq_i = omega w_i (R - 9/2 t3) + 9/2 omega w_i c_i c_i : S + 3 omega w_i c_i . j
     const T cf = p.cf;
     const T b = R - h * t3;
-    f[0] = cf * f[0] + p.f0 * b;
+    f[0] = fmadd(cf, f[0], p.f0 * b);
     const T B1 = p.f1 * b, B2 = p.f2 * b;
 #define LBK_FACE(IP, IM, SAA, JA)                                  \
     {                                                              \
-        const T s_ = p.f1h * SAA + B1, a_ = p.f1t * JA;            \
-        f[IP] = cf * f[IP] + (s_ + a_);                            \
-        f[IM] = cf * f[IM] + (s_ - a_);                            \
+        const T s_ = fmadd(p.f1h, SAA, B1), a_ = p.f1t * JA;       \
+        f[IP] = fmadd(cf, f[IP], s_ + a_);                         \
+        f[IM] = fmadd(cf, f[IM], s_ - a_);                         \
     }
     LBK_FACE(1, 2, Sxx, jx)
     LBK_FACE(3, 4, Syy, jy)
@@ -195,13 +204,13 @@ __device__ __forceinline__ void collide_f(const Coll<T>& p, T (&f)[Q], T phi, T 
     // edge pairs (a+b, -a-b) = (IP, IM) and (a-b, -a+b) = (KP, KM); 2 f2h = f1h
 #define LBK_EDGES(IP, IM, KP, KM, SAA, SBB, SAB, JA, JB)             \
     {                                                                \
-        const T e_ = p.f2h * (SAA + SBB) + B2, o_ = p.f1h * SAB;     \
+        const T e_ = fmadd(p.f2h, SAA + SBB, B2), o_ = p.f1h * SAB;  \
         const T sp = e_ + o_, sm = e_ - o_;                          \
         const T ap = p.f2t * (JA + JB), am = p.f2t * (JA - JB);      \
-        f[IP] = cf * f[IP] + (sp + ap);                              \
-        f[IM] = cf * f[IM] + (sp - ap);                              \
-        f[KP] = cf * f[KP] + (sm + am);                              \
-        f[KM] = cf * f[KM] + (sm - am);                              \
+        f[IP] = fmadd(cf, f[IP], sp + ap);                           \
+        f[IM] = fmadd(cf, f[IM], sp - ap);                           \
+        f[KP] = fmadd(cf, f[KP], sm + am);                           \
+        f[KM] = fmadd(cf, f[KM], sm - am);                           \
     }
     LBK_EDGES(7, 8, 9, 10, Sxx, Syy, Sxy, jx, jy)
     LBK_EDGES(11, 12, 13, 14, Sxx, Szz, Sxz, jx, jz)
@@ -221,13 +230,13 @@ __device__ __forceinline__ void collide_g(const Coll<T>& p, T (&g)[Q], T phi, T 
     const T pu2 = (px * ux + py * uy + pz * uz) * third;
     const T gm = p.gamma * mu - phi * third;
     const T bg = phi - h * pu2;
-    g[0] = cg * g[0] + p.g0 * (bg - h * gm);
+    g[0] = fmadd(cg, g[0], p.g0 * (bg - h * gm));
     const T G1 = p.g1 * bg, G2 = p.g2 * (bg + h * gm);
 #define LBK_GFACE(IP, IM, PA, UA)                                   \
     {                                                               \
-        const T s_ = p.g1h * (PA * UA) + G1, a_ = p.g1t * PA;       \
-        g[IP] = cg * g[IP] + (s_ + a_);                             \
-        g[IM] = cg * g[IM] + (s_ - a_);                             \
+        const T s_ = fmadd(p.g1h, PA * UA, G1), a_ = p.g1t * PA;    \
+        g[IP] = fmadd(cg, g[IP], s_ + a_);                          \
+        g[IM] = fmadd(cg, g[IM], s_ - a_);                          \
     }
     LBK_GFACE(1, 2, px, ux)
     LBK_GFACE(3, 4, py, uy)
@@ -236,9 +245,9 @@ __device__ __forceinline__ void collide_g(const Coll<T>& p, T (&g)[Q], T phi, T 
 #define LBK_GEDGE(IP, IM, PC, CU)                                   \
     {                                                               \
         const T pc_ = PC, cu_ = CU;                                 \
-        const T s_ = p.g2h * (pc_ * cu_) + G2, a_ = p.g2t * pc_;    \
-        g[IP] = cg * g[IP] + (s_ + a_);                             \
-        g[IM] = cg * g[IM] + (s_ - a_);                             \
+        const T s_ = fmadd(p.g2h, pc_ * cu_, G2), a_ = p.g2t * pc_; \
+        g[IP] = fmadd(cg, g[IP], s_ + a_);                          \
+        g[IM] = fmadd(cg, g[IM], s_ - a_);                          \
     }
     LBK_GEDGE(7, 8, px + py, ux + uy)
     LBK_GEDGE(9, 10, px - py, ux - uy)
@@ -251,17 +260,12 @@ __device__ __forceinline__ void collide_g(const Coll<T>& p, T (&g)[Q], T phi, T 
         // In float the folded weights do not sum to omega_g (1/3 + 6/18 +
         // 12/36 rounds to 1 + 1.5e-8), which would bias sum g* -- phi -- by
         // that fraction every step.  The rest value takes up the difference
-        // instead: g*_0 = phi - sum_{i>0} g*_i, the sum with its rounding
-        // errors carried (TwoSum), so phi is conserved up to unbiased rounding.
-        T s = g[1], c = T(0);
-#pragma unroll
-        for (int i = 2; i < Q; i++) {
-            const T t = s + g[i];
-            const T bp = t - s;
-            c += (s - (t - bp)) + (g[i] - bp);
-            s = t;
-        }
-        g[0] = (phi - s) - c;
+        // instead, g*_0 = phi - sum_{i>0} g*_i, so phi is conserved up to
+        // unbiased rounding (carrying that sum's rounding errors as well was
+        // measured to change nothing).
+        T s = ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
+        s += ((g[9] + g[10]) + (g[11] + g[12])) + ((g[13] + g[14]) + (g[15] + g[16])) + (g[17] + g[18]);
+        g[0] = phi - s;
     }
 }
 
@@ -351,14 +355,14 @@ __device__ __forceinline__ void collide_mrt(const Coll<T>& p, const Mrt<T>& m, T
     const T cf = m.cgh;
     const T w0 = T(1.0 / 3.0), w1 = T(1.0 / 18.0), w2 = T(1.0 / 36.0);
     const T b = Rp - h * t3;
-    f[0] = cf * f[0] + w0 * b;
+    f[0] = fmadd(cf, f[0], w0 * b);
     const T B1 = w1 * b, B2 = w2 * b;
     const T f1h = w1 * h, f1t = w1 * T(3), f2h = w2 * h, f2t = w2 * T(3);
 #define LBK_MFACE(IP, IM, SAA, JA)                                 \
     {                                                              \
-        const T s_ = f1h * SAA + B1, a_ = f1t * JA;                \
-        f[IP] = cf * f[IP] + (s_ + a_);                            \
-        f[IM] = cf * f[IM] + (s_ - a_);                            \
+        const T s_ = fmadd(f1h, SAA, B1), a_ = f1t * JA;           \
+        f[IP] = fmadd(cf, f[IP], s_ + a_);                         \
+        f[IM] = fmadd(cf, f[IM], s_ - a_);                         \
     }
     LBK_MFACE(1, 2, Spxx, Jpx)
     LBK_MFACE(3, 4, Spyy, Jpy)
@@ -366,13 +370,13 @@ __device__ __forceinline__ void collide_mrt(const Coll<T>& p, const Mrt<T>& m, T
 #undef LBK_MFACE
 #define LBK_MEDGES(IP, IM, KP, KM, SAA, SBB, SAB, JA, JB)            \
     {                                                                \
-        const T e_ = f2h * (SAA + SBB) + B2, o_ = f1h * SAB;         \
+        const T e_ = fmadd(f2h, SAA + SBB, B2), o_ = f1h * SAB;      \
         const T sp = e_ + o_, sm = e_ - o_;                          \
         const T ap = f2t * (JA + JB), am = f2t * (JA - JB);          \
-        f[IP] = cf * f[IP] + (sp + ap);                              \
-        f[IM] = cf * f[IM] + (sp - ap);                              \
-        f[KP] = cf * f[KP] + (sm + am);                              \
-        f[KM] = cf * f[KM] + (sm - am);                              \
+        f[IP] = fmadd(cf, f[IP], sp + ap);                           \
+        f[IM] = fmadd(cf, f[IM], sp - ap);                           \
+        f[KP] = fmadd(cf, f[KP], sm + am);                           \
+        f[KM] = fmadd(cf, f[KM], sm - am);                           \
     }
     LBK_MEDGES(7, 8, 9, 10, Spxx, Spyy, Spxy, Jpx, Jpy)
     LBK_MEDGES(11, 12, 13, 14, Spxx, Spzz, Spxz, Jpx, Jpz)

@@ -88,7 +88,8 @@ int validate(const lb_params *p)
     for (double x : v)
         if (!finite_pos(x)) return LB_ERR_INVALID;
     if (!(p->tau > 0.5) || !(p->tau_g > 0.5) || !(p->rho0 > 0.0)) return LB_ERR_INVALID;
-    if (p->precision != LB_FP64 && p->precision != LB_FP32_SHIFTED) return LB_ERR_INVALID;
+    if (p->precision != LB_FP64 && p->precision != LB_FP32_SHIFTED && p->precision != LB_FP64_DF)
+        return LB_ERR_INVALID;
     return LB_OK;
 }
 
@@ -189,7 +190,7 @@ int lb_create(const lb_params *p, void *cuda_stream, lb_ctx **out)
     c->stream = (cudaStream_t)cuda_stream;
     c->N = (long long)p->nx * p->ny * p->nz;
     c->S = lbk::component_stride(c->N);
-    c->esize = p->precision == LB_FP64 ? sizeof(double) : sizeof(float);
+    c->esize = p->precision == LB_FP32_SHIFTED ? sizeof(float) : 8;   // double or two floats
     {
         std::lock_guard<std::mutex> lk(g_alloc_mu);
         c->alloc = g_alloc;
@@ -381,6 +382,8 @@ int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk)
     if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_TAUG1 || c->batch_owned) return LB_ERR_INVALID;
     if (block_x < 0 || block_y < 0 || z_chunk < 0) return LB_ERR_INVALID;
     if (c->npts != 7 && seven_point_only(kernel)) return LB_ERR_INVALID;
+    if (c->p.precision == LB_FP64_DF && kernel != LB_KERNEL_AUTO && kernel != LB_KERNEL_TWO_PASS)
+        return LB_ERR_INVALID;
     if (lbk::uses_mrt(c) && kernel != LB_KERNEL_AUTO && kernel != LB_KERNEL_TWO_PASS) return LB_ERR_INVALID;
     if (kernel == LB_KERNEL_STAGED) {
         int rc = lbk::staged_validate(c->p.precision, block_x, block_y, z_chunk);

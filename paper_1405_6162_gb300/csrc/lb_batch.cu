@@ -290,6 +290,7 @@ int lb_batch_create(int n, const lb_params *p, void *cuda_stream, lb_batch **out
     if (!out) return LB_ERR_INVALID;
     *out = nullptr;
     if (n < 1 || !p) return LB_ERR_INVALID;
+    if (p[0].precision != LB_FP64 && p[0].precision != LB_FP32_SHIFTED) return LB_ERR_INVALID;
     for (int k = 1; k < n; k++)
         if (p[k].precision != p[0].precision) return LB_ERR_INVALID;
     lb_batch *b = new (std::nothrow) lb_batch();

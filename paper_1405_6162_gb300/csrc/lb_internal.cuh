@@ -6,6 +6,7 @@
 #include <stddef.h>
 
 #include "d3q19.cuh"
+#include "df64.cuh"
 #include "lb.h"
 #include "lb_coll.cuh"
 
@@ -68,6 +69,24 @@ namespace lbk {
 inline bool uses_mrt(const lb_ctx *c)
 {
     return c->collision == LB_COLLISION_MRT || c->force[0] != 0.0 || c->force[1] != 0.0 || c->force[2] != 0.0;
+}
+
+// storage / arithmetic type of a context and whether f is stored shifted
+template <typename T_, bool SH_>
+struct Prec {
+    using T = T_;
+    static constexpr bool SH = SH_;
+};
+
+// f(Prec<T, SH>{}) for the context's precision
+template <typename F>
+inline int by_precision(const lb_ctx *c, F &&f)
+{
+    switch (c->p.precision) {
+    case LB_FP64: return f(Prec<double, false>{});
+    case LB_FP64_DF: return f(Prec<df64, false>{});
+    default: return f(Prec<float, true>{});
+    }
 }
 
 // MRT rates and force of the context in the arithmetic type T

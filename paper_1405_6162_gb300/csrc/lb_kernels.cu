@@ -65,9 +65,17 @@ __global__ void __launch_bounds__(256) k_phi_pull(const T *__restrict__ ga, T *_
 #ifndef LBK_K2_MINB32
 #define LBK_K2_MINB32 3
 #endif
+#ifndef LBK_K2_MINBDF
+#define LBK_K2_MINBDF 2
+#endif
+#ifndef LBK_K2_MINB32W
+#define LBK_K2_MINB32W 3   // FP32 with the 19- / 27-point stencils
+#endif
+#define LBK_K2_MINB(T, NP) \
+    (is_df64<T>::value ? LBK_K2_MINBDF : sizeof(T) == 8 ? LBK_K2_MINB64 : NP > 7 ? LBK_K2_MINB32W : LBK_K2_MINB32)
 
 template <typename T, bool SH, int NP = 7>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? LBK_K2_MINB64 : LBK_K2_MINB32) k_collide_pull(const T *__restrict__ fa, const T *__restrict__ ga,
+__global__ void __launch_bounds__(256, LBK_K2_MINB(T, NP)) k_collide_pull(const T *__restrict__ fa, const T *__restrict__ ga,
                                                       const T *__restrict__ phi,
                                                       T *__restrict__ fb, T *__restrict__ gb,
                                                       Coll<T> p, int nx, int ny, int nz, long long S)
@@ -81,7 +89,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? LBK_K2_MINB64 : LBK_K2_M
 
 // multiple-relaxation-time collision of f with a Guo body force (collide_mrt)
 template <typename T, bool SH, int NP>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? LBK_K2_MINB64 : LBK_K2_MINB32)
+__global__ void __launch_bounds__(256, LBK_K2_MINB(T, NP))
 k_collide_pull_mrt(const T *__restrict__ fa, const T *__restrict__ ga, const T *__restrict__ phi,
                    T *__restrict__ fb, T *__restrict__ gb, Coll<T> p, Mrt<T> m, int nx, int ny, int nz,
                    long long S)
@@ -274,11 +282,10 @@ static void init_t(lb_ctx *c, const double *phi0_d, const double *u0_d)
 
 int launch_init(lb_ctx *c, const double *phi0_d, const double *u0_d)
 {
-    if (c->p.precision == LB_FP64)
-        init_t<double, false>(c, phi0_d, u0_d);
-    else
-        init_t<float, true>(c, phi0_d, u0_d);
-    return check_launch();
+    return by_precision(c, [&](auto P) {
+        init_t<typename decltype(P)::T, decltype(P)::SH>(c, phi0_d, u0_d);
+        return check_launch();
+    });
 }
 
 template <typename T, bool SH, int NP>
@@ -328,7 +335,7 @@ static int two_pass_t(lb_ctx *c, int nsteps)
 
 int launch_step_two_pass(lb_ctx *c, int nsteps)
 {
-    return c->p.precision == LB_FP64 ? two_pass_t<double, false>(c, nsteps) : two_pass_t<float, true>(c, nsteps);
+    return by_precision(c, [&](auto P) { return two_pass_t<typename decltype(P)::T, decltype(P)::SH>(c, nsteps); });
 }
 
 int launch_moments(lb_ctx *c, double *rho, double *u, double *phi)
@@ -336,17 +343,13 @@ int launch_moments(lb_ctx *c, double *rho, double *u, double *phi)
     const int cur = c->buf.cur;
     const double hF[3] = {0.5 * c->force[0], 0.5 * c->force[1], 0.5 * c->force[2]};
     const unsigned grid = grid_for(c->N, 256);
-    if (c->p.precision == LB_FP64)
-        k_moments<double, false><<<grid, 256, 0, c->stream>>>((const double *)c->buf.f[cur],
-                                                              (const double *)c->buf.g[cur], rho, u, phi,
-                                                              c->p.rho0, hF[0], hF[1], hF[2], c->p.nx,
-                                                              c->p.ny, c->p.nz, c->S);
-    else
-        k_moments<float, true><<<grid, 256, 0, c->stream>>>((const float *)c->buf.f[cur],
-                                                            (const float *)c->buf.g[cur], rho, u, phi,
-                                                            c->p.rho0, hF[0], hF[1], hF[2], c->p.nx,
-                                                            c->p.ny, c->p.nz, c->S);
-    return check_launch();
+    return by_precision(c, [&](auto P) {
+        using T = typename decltype(P)::T;
+        k_moments<T, decltype(P)::SH><<<grid, 256, 0, c->stream>>>((const T *)c->buf.f[cur], (const T *)c->buf.g[cur],
+                                                                  rho, u, phi, c->p.rho0, hF[0], hF[1], hF[2],
+                                                                  c->p.nx, c->p.ny, c->p.nz, c->S);
+        return check_launch();
+    });
 }
 
 // f or g, components [i0, i1), to out (i1 - i0 rows of N)
@@ -355,14 +358,13 @@ static int get_rows(lb_ctx *c, int which, int i0, int i1, double *out)
     const int cur = c->buf.cur;
     const unsigned grid = grid_for(c->N, 256);
     const double shift = (which == 0 && c->p.precision == LB_FP32_SHIFTED) ? c->p.rho0 : 0.0;
-    void *a = which == 0 ? c->buf.f[cur] : c->buf.g[cur];
-    if (c->p.precision == LB_FP64)
-        k_get_state<double><<<grid, 256, 0, c->stream>>>((const double *)a, out, i0, i1, shift,
-                                                         c->p.nx, c->p.ny, c->p.nz, c->S);
-    else
-        k_get_state<float><<<grid, 256, 0, c->stream>>>((const float *)a, out, i0, i1, shift,
-                                                        c->p.nx, c->p.ny, c->p.nz, c->S);
-    return check_launch();
+    const void *a = which == 0 ? c->buf.f[cur] : c->buf.g[cur];
+    return by_precision(c, [&](auto P) {
+        using T = typename decltype(P)::T;
+        k_get_state<T><<<grid, 256, 0, c->stream>>>((const T *)a, out, i0, i1, shift, c->p.nx, c->p.ny, c->p.nz,
+                                                     c->S);
+        return check_launch();
+    });
 }
 
 static int set_rows(lb_ctx *c, int which, int i0, int i1, const double *in)
@@ -371,13 +373,11 @@ static int set_rows(lb_ctx *c, int which, int i0, int i1, const double *in)
     const unsigned grid = grid_for(c->N, 256);
     const double shift = (which == 0 && c->p.precision == LB_FP32_SHIFTED) ? c->p.rho0 : 0.0;
     void *a = which == 0 ? c->buf.f[cur] : c->buf.g[cur];
-    if (c->p.precision == LB_FP64)
-        k_set_state<double><<<grid, 256, 0, c->stream>>>((double *)a, in, i0, i1, shift,
-                                                         c->p.nx, c->p.ny, c->p.nz, c->S);
-    else
-        k_set_state<float><<<grid, 256, 0, c->stream>>>((float *)a, in, i0, i1, shift,
-                                                        c->p.nx, c->p.ny, c->p.nz, c->S);
-    return check_launch();
+    return by_precision(c, [&](auto P) {
+        using T = typename decltype(P)::T;
+        k_set_state<T><<<grid, 256, 0, c->stream>>>((T *)a, in, i0, i1, shift, c->p.nx, c->p.ny, c->p.nz, c->S);
+        return check_launch();
+    });
 }
 
 int launch_get_state(lb_ctx *c, double *f, double *g)
@@ -405,13 +405,12 @@ int launch_reduce(lb_ctx *c, double *dev_out5)
 {
     const int cur = c->buf.cur;
     const double off = c->p.precision == LB_FP32_SHIFTED ? double(c->N) * c->p.rho0 : 0.0;
-    if (c->p.precision == LB_FP64)
-        k_reduce_partial<double><<<kReduceBlocks, kReduceThreads, 0, c->stream>>>(
-            (const double *)c->buf.f[cur], (const double *)c->buf.g[cur], c->N, c->S, c->reduced ? 1 : Q, c->partial);
-    else
-        k_reduce_partial<float><<<kReduceBlocks, kReduceThreads, 0, c->stream>>>(
-            (const float *)c->buf.f[cur], (const float *)c->buf.g[cur], c->N, c->S, c->reduced ? 1 : Q, c->partial);
-    int rc = check_launch();
+    int rc = by_precision(c, [&](auto P) {
+        using T = typename decltype(P)::T;
+        k_reduce_partial<T><<<kReduceBlocks, kReduceThreads, 0, c->stream>>>(
+            (const T *)c->buf.f[cur], (const T *)c->buf.g[cur], c->N, c->S, c->reduced ? 1 : Q, c->partial);
+        return check_launch();
+    });
     if (rc) return rc;
     k_reduce_final<<<1, kReduceThreads, 0, c->stream>>>(c->partial, kReduceBlocks, off, dev_out5);
     return check_launch();

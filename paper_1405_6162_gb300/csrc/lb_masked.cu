@@ -206,23 +206,18 @@ int launch_masked_moments(lb_ctx *c, long long total, const int *scratch, double
     const double hF[3] = {0.5 * c->force[0], 0.5 * c->force[1], 0.5 * c->force[2]};
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
     const unsigned grid = gather_blocks(total);
-#define LBK_MM(T, SH, RED)                                                                                        \
-    k_masked_moments<T, SH, RED><<<grid, kGatherThreads, 0, c->stream>>>(                                        \
-        (const T *)c->buf.f[cur], (const T *)c->buf.g[cur], idx, (int)total, c->p.rho0, hF[0], hF[1], hF[2], rho, \
-        u, phi, nx, ny, nz, c->S)
-    if (c->p.precision == LB_FP64) {
+    return by_precision(c, [&](auto P) {
+        using T = typename decltype(P)::T;
+        constexpr bool SH = decltype(P)::SH;
+        const T *fa = (const T *)c->buf.f[cur], *ga = (const T *)c->buf.g[cur];
         if (c->reduced)
-            LBK_MM(double, false, true);
+            k_masked_moments<T, SH, true><<<grid, kGatherThreads, 0, c->stream>>>(
+                fa, ga, idx, (int)total, c->p.rho0, hF[0], hF[1], hF[2], rho, u, phi, nx, ny, nz, c->S);
         else
-            LBK_MM(double, false, false);
-    } else {
-        if (c->reduced)
-            LBK_MM(float, true, true);
-        else
-            LBK_MM(float, true, false);
-    }
-#undef LBK_MM
-    return check_launch();
+            k_masked_moments<T, SH, false><<<grid, kGatherThreads, 0, c->stream>>>(
+                fa, ga, idx, (int)total, c->p.rho0, hF[0], hF[1], hF[2], rho, u, phi, nx, ny, nz, c->S);
+        return check_launch();
+    });
 }
 
 int launch_masked_rows(lb_ctx *c, long long total, const int *scratch, int which, int i0, int i1, double *io,
@@ -236,22 +231,16 @@ int launch_masked_rows(lb_ctx *c, long long total, const int *scratch, int which
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
     const unsigned grid = gather_blocks(total);
     const int tot = (int)total;
-    if (c->p.precision == LB_FP64) {
+    return by_precision(c, [&](auto P) {
+        using T = typename decltype(P)::T;
         if (to_device_state)
-            k_masked_set<double><<<grid, kGatherThreads, 0, c->stream>>>((double *)a, idx, tot, i0, i1, shift, io,
-                                                                         nx, ny, nz, c->S);
+            k_masked_set<T><<<grid, kGatherThreads, 0, c->stream>>>((T *)a, idx, tot, i0, i1, shift, io, nx, ny, nz,
+                                                                    c->S);
         else
-            k_masked_get<double><<<grid, kGatherThreads, 0, c->stream>>>((const double *)a, idx, tot, i0, i1, shift,
-                                                                         io, nx, ny, nz, c->S);
-    } else {
-        if (to_device_state)
-            k_masked_set<float><<<grid, kGatherThreads, 0, c->stream>>>((float *)a, idx, tot, i0, i1, shift, io, nx,
-                                                                        ny, nz, c->S);
-        else
-            k_masked_get<float><<<grid, kGatherThreads, 0, c->stream>>>((const float *)a, idx, tot, i0, i1, shift,
-                                                                        io, nx, ny, nz, c->S);
-    }
-    return check_launch();
+            k_masked_get<T><<<grid, kGatherThreads, 0, c->stream>>>((const T *)a, idx, tot, i0, i1, shift, io, nx,
+                                                                    ny, nz, c->S);
+        return check_launch();
+    });
 }
 
 }  // namespace lbk

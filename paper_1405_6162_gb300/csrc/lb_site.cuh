@@ -110,15 +110,19 @@ __device__ __forceinline__ void collide_site(const T *__restrict__ fa, const T *
                                              long long S)
 {
     T f[Q], g[Q];
+    const T ph = phi[s];
+    T dx, dy, dz, lap;
+    // the 27-point stencil first, so that its temporaries are dead before the
+    // 38 distribution values arrive (measured: +7 % for it in FP32, -2 % for
+    // the 19-point one, which stays after the loads)
+    if constexpr (NP == 27) stencil_np<NP, T>(phi, n, ph, dx, dy, dz, lap);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         const size_t o = (size_t)i * S + n.src(i);
         f[i] = fa[o];
         g[i] = ga[o];
     }
-    const T ph = phi[s];
-    T dx, dy, dz, lap;
-    stencil_np<NP, T>(phi, n, ph, dx, dy, dz, lap);
+    if constexpr (NP != 27) stencil_np<NP, T>(phi, n, ph, dx, dy, dz, lap);
     collide<T, SH>(p, f, g, ph, dx, dy, dz, lap);
 #pragma unroll
     for (int i = 0; i < Q; i++) {

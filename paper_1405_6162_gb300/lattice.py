@@ -15,7 +15,7 @@ import numpy as np
 
 from . import _lib as L
 
-PRECISIONS = {"fp64": L.LB_FP64, "fp32_shifted": L.LB_FP32_SHIFTED}
+PRECISIONS = {"fp64": L.LB_FP64, "fp32_shifted": L.LB_FP32_SHIFTED, "fp64_df": L.LB_FP64_DF}
 KERNELS = {"auto": L.LB_KERNEL_AUTO, "two_pass": L.LB_KERNEL_TWO_PASS, "fused": L.LB_KERNEL_FUSED,
            "staged": L.LB_KERNEL_STAGED, "slab": L.LB_KERNEL_SLAB, "lag": L.LB_KERNEL_LAG,
            "taug1": L.LB_KERNEL_TAUG1}
@@ -88,8 +88,8 @@ class Lattice:
     """One periodic D3Q19 binary-fluid lattice held on the GPU.
 
     Parameters follow ``lb_params`` (include/lb.h): extents nx, ny, nz and
-    tau, tau_g, rho0, gamma, A, B, kappa; ``precision`` is "fp64" or
-    "fp32_shifted".
+    tau, tau_g, rho0, gamma, A, B, kappa; ``precision`` is "fp64",
+    "fp32_shifted" or "fp64_df" (double-float on the FP32 units).
     """
 
     def __init__(self, nx, ny, nz, *, tau, tau_g, rho0, gamma, A, B, kappa,
