@@ -373,6 +373,16 @@ int lb_batch_sync(lb_batch *b);
  * always co-resident).  Paper: TPB and VVL tuning, Sec. III.C and IV. */
 int lb_batch_set_launch(lb_batch *b, int threads, int ctas_per_sm);
 
+/* Form of the ensemble's step: 0 = the general two-pass step (default), 1 =
+ * the tau_g = 1 reduced form of LB_KERNEL_TAUG1 for every lattice (g kept as
+ * phi and (gmh, u); the collide pass over the same site blocks, then the phi
+ * pass over tiles of 30 x-columns, 32/threads-per-CTA warps of rows and 8
+ * z planes).  Converts every member's stored state (lb_get_state /
+ * lb_moments of a member report the same state before and after).
+ * LB_ERR_INVALID unless every lattice has tau_g == 1.  Synchronises.
+ * Paper: no counterpart (the tau_g = 1 form of the collision). */
+int lb_batch_set_form(lb_batch *b, int reduced);
+
 /* n lattices, work items per pass, CTAs in the grid, threads per CTA. */
 int lb_batch_size(const lb_batch *b, int *n, int *work_items, int *grid, int *threads);
 

@@ -82,6 +82,7 @@ SIGNATURES = {
     "lb_batch_run": (_I, [_P, _I]),
     "lb_batch_sync": (_I, [_P]),
     "lb_batch_set_launch": (_I, [_P, _I, _I]),
+    "lb_batch_set_form": (_I, [_P, _I]),
     "lb_batch_size": (_I, [_P, _P, _P, _P, _P]),
     "lb_batch_set_wait_timeout": (_I, [_P, ctypes.c_longlong]),
     "lb_batch_debug_skip_arrival": (_I, [_P, _I]),

@@ -73,6 +73,10 @@ class Batch:
     def sync(self):
         L.check(L.lib().lb_batch_sync(self.handle), "lb_batch_sync")
 
+    def set_form(self, form: str = "general"):
+        """"general" two-pass step or the tau_g = 1 "taug1" reduced form."""
+        L.check(L.lib().lb_batch_set_form(self.handle, {"general": 0, "taug1": 1}[form]), "lb_batch_set_form")
+
     def set_launch(self, threads: int = 256, ctas_per_sm: int = 0):
         L.check(L.lib().lb_batch_set_launch(self.handle, int(threads), int(ctas_per_sm)), "lb_batch_set_launch")
 

@@ -7,7 +7,10 @@
 // cooperative launch) walks that list twice per timestep -- the phi pass,
 // then the collide/stream pass -- with a grid-wide barrier after each, and
 // loops over the timesteps inside the kernel.  The per-site arithmetic is the
-// default step's (lb_site.cuh).  The launch (with a reset of the barrier
+// default step's (lb_site.cuh), or, for an ensemble whose lattices all have
+// tau_g = 1 and that was switched to the reduced form, the reduced form's two
+// passes (lb_t1.cuh): the collide pass over the same (lattice, block) items,
+// then the phi pass over (lattice, x block, warp group, z run) tiles.  The launch (with a reset of the barrier
 // state) is captured once per (steps, parity) into a CUDA graph and replayed.
 // The block size and CTAs per SM -- the paper's TPB and its per-thread work
 // (targetDP Sec. III.C) -- are the knobs the autotuner sets.
@@ -21,6 +24,7 @@
 #include "d3q19.cuh"
 #include "lb_internal.cuh"
 #include "lb_site.cuh"
+#include "lb_t1.cuh"
 
 namespace lbk {
 
@@ -44,12 +48,15 @@ constexpr int kBatchMaxThreads64 = 256;   // FP64: more registers per thread
 template <typename T>
 struct LatDesc {
     int nx, ny, nz;
+    int kzc;   // reduced form: z planes per phi-pass tile
     long long N, S;
     const T *f[2];
     const T *g[2];
     T *phi;
     Coll<T> p;
 };
+
+constexpr int kBatchT1Kzc = 8;   // z run of a reduced-form phi tile in the ensemble
 
 struct GridBarrier {
     unsigned int count;
@@ -97,15 +104,42 @@ __device__ bool grid_sync(GridBarrier *bar, unsigned int nblocks, long long time
     return !*s_fail;
 }
 
-template <typename T, bool SH>
+template <typename T, bool SH, bool RED>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? kBatchMaxThreads64 : kBatchMaxThreads,
                                   sizeof(T) == 8 ? LBK_BATCH_MINB64 : LBK_BATCH_MINB32) k_batch(const LatDesc<T> *__restrict__ lats,
-                                                            const int2 *__restrict__ work, int nwork, int nsteps,
-                                                            int parity0, GridBarrier *bar, unsigned int *err,
-                                                            long long timeout_ns, int debug_skip_arrival)
+                                                            const int2 *__restrict__ work, int nwork,
+                                                            const int4 *__restrict__ work_t1, int nwork_t1,
+                                                            int nsteps, int parity0, GridBarrier *bar,
+                                                            unsigned int *err, long long timeout_ns,
+                                                            int debug_skip_arrival)
 {
     __shared__ int s_fail;
     if (threadIdx.x == 0) s_fail = 0;
+    if constexpr (RED) {
+        constexpr int KY = PhiTile<T>::KY;
+        const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int t = 0; t < nsteps; t++) {
+            const int a = (parity0 + t) & 1;
+            for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+                const int2 it = work[w];
+                const LatDesc<T> &L = lats[it.x];
+                const long long s = (long long)it.y * blockDim.x + threadIdx.x;
+                if (s < L.N)
+                    t1_collide_site<T, SH, 7>(L.f[a], const_cast<T *>(L.g[a]), const_cast<T *>(L.f[1 - a]), L.p,
+                                              L.nx, L.ny, L.nz, L.S, (int)s);
+            }
+            if (debug_skip_arrival && blockIdx.x == 0) return;   // test hook: this CTA never arrives
+            if (!grid_sync(bar, gridDim.x, timeout_ns, err, &s_fail)) return;
+            for (int w = blockIdx.x; w < nwork_t1; w += gridDim.x) {
+                const int4 it = work_t1[w];   // (lattice, x block, warp group, z run)
+                const LatDesc<T> &L = lats[it.x];
+                t1_phi_tile<T, KY>(L.g[a], const_cast<T *>(L.g[1 - a]), L.nx, L.ny, L.nz, L.kzc, L.S, it.y,
+                                   (it.z * warps + warp) * KY, it.w, lane);
+            }
+            if (!grid_sync(bar, gridDim.x, timeout_ns, err, &s_fail)) return;
+        }
+        return;
+    }
     for (int t = 0; t < nsteps; t++) {
         const int a = (parity0 + t) & 1;
         for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
@@ -146,6 +180,9 @@ struct lb_batch {
     void *d_lats = nullptr;
     int2 *d_work = nullptr;
     int nwork = 0;
+    int4 *d_work_t1 = nullptr;                 // reduced form: phi-pass tiles
+    int nwork_t1 = 0;
+    int reduced = 0;                           // all lattices in the tau_g = 1 reduced form
     lbk::GridBarrier *d_bar = nullptr;
     unsigned int *d_err = nullptr;
     int threads = 256;                         // sites per work item = threads per CTA
@@ -170,6 +207,7 @@ int batch_tables(lb_batch *b)
 {
     std::vector<lbk::LatDesc<T>> L(b->n);
     std::vector<int2> work;
+    std::vector<int4> work_t1;
     for (int k = 0; k < b->n; k++) {
         lb_ctx *c = b->ctx[k];
         L[k].nx = c->p.nx;
@@ -183,27 +221,45 @@ int batch_tables(lb_batch *b)
         }
         L[k].phi = (T *)c->phi;
         L[k].p = lbk::make_coll<T>(c->p);
+        L[k].kzc = c->p.nz < lbk::kBatchT1Kzc ? c->p.nz : lbk::kBatchT1Kzc;
         const long long nb = (c->N + b->threads - 1) / b->threads;
         for (long long j = 0; j < nb; j++) work.push_back(make_int2(k, (int)j));
+        if (b->reduced) {
+            const int rows = (b->threads / 32) * lbk::PhiTile<T>::KY;   // y rows of one warp group
+            const int gx = (c->p.nx + lbk::kPhiOut - 1) / lbk::kPhiOut, gy = (c->p.ny + rows - 1) / rows;
+            const int gz = (c->p.nz + L[k].kzc - 1) / L[k].kzc;
+            for (int z = 0; z < gz; z++)
+                for (int y = 0; y < gy; y++)
+                    for (int x = 0; x < gx; x++) work_t1.push_back(make_int4(k, x, y, z));
+        }
     }
     cudaFree(b->d_lats);
     cudaFree(b->d_work);
+    cudaFree(b->d_work_t1);
     b->d_lats = nullptr;
     b->d_work = nullptr;
+    b->d_work_t1 = nullptr;
     int rc = lbk::cuda_status(cudaMalloc(&b->d_lats, sizeof(lbk::LatDesc<T>) * b->n));
     if (!rc) rc = lbk::cuda_status(cudaMalloc(&b->d_work, sizeof(int2) * work.size()));
     if (!rc) rc = lbk::cuda_status(cudaMemcpy(b->d_lats, L.data(), sizeof(lbk::LatDesc<T>) * b->n,
                                               cudaMemcpyHostToDevice));
     if (!rc) rc = lbk::cuda_status(cudaMemcpy(b->d_work, work.data(), sizeof(int2) * work.size(),
                                               cudaMemcpyHostToDevice));
+    if (!rc && !work_t1.empty()) {
+        rc = lbk::cuda_status(cudaMalloc(&b->d_work_t1, sizeof(int4) * work_t1.size()));
+        if (!rc) rc = lbk::cuda_status(cudaMemcpy(b->d_work_t1, work_t1.data(), sizeof(int4) * work_t1.size(),
+                                                  cudaMemcpyHostToDevice));
+    }
     b->nwork = (int)work.size();
+    b->nwork_t1 = (int)work_t1.size();
     if (rc) return rc;
     // co-resident grid
     int dev = 0, sms = 0, per_sm = 0;
     rc = lbk::cuda_status(cudaGetDevice(&dev));
     if (!rc) rc = lbk::cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (!rc) rc = lbk::cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbk::k_batch<T, SH>,
-                                                                                 b->threads, 0));
+    if (!rc)
+        rc = lbk::cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, b->reduced ? lbk::k_batch<T, SH, true> : lbk::k_batch<T, SH, false>, b->threads, 0));
     if (rc) return rc;
     if (per_sm < 1) return LB_ERR_INVALID;
     const int use = b->ctas_per_sm > 0 && b->ctas_per_sm < per_sm ? b->ctas_per_sm : per_sm;
@@ -235,8 +291,10 @@ int capture(lb_batch *b, int nsteps, int parity, cudaGraphExec_t *out)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const lbk::LatDesc<T> *lats = (const lbk::LatDesc<T> *)b->d_lats;
-    const cudaError_t le = cudaLaunchKernelEx(&cfg, lbk::k_batch<T, SH>, lats, (const int2 *)b->d_work, b->nwork,
-                                              nsteps, parity, b->d_bar, b->d_err, b->timeout_ns, b->debug_skip);
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, b->reduced ? lbk::k_batch<T, SH, true> : lbk::k_batch<T, SH, false>,
+                                              lats, (const int2 *)b->d_work, b->nwork, (const int4 *)b->d_work_t1,
+                                              b->nwork_t1, nsteps, parity, b->d_bar, b->d_err, b->timeout_ns,
+                                              b->debug_skip);
     const cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
     rc = lbk::cuda_status(le != cudaSuccess ? le : ce);
     if (!rc) rc = lbk::cuda_status(cudaGraphInstantiate(out, graph, 0));
@@ -276,6 +334,7 @@ void lb_batch_destroy(lb_batch *b)
     }
     cudaFree(b->d_lats);
     cudaFree(b->d_work);
+    cudaFree(b->d_work_t1);
     cudaFree(b->d_bar);
     cudaFree(b->d_err);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
@@ -385,8 +444,29 @@ int lb_batch_run(lb_batch *b, int nsteps)
     if (!rc) rc = lbk::cuda_status(cudaStreamWaitEvent(b->user_stream, b->ev_out, 0));
     if (rc) return rc;
     b->parity ^= (nsteps & 1);
-    for (lb_ctx *c : b->ctx) c->buf.cur = b->parity;
+    for (lb_ctx *c : b->ctx) {
+        c->buf.cur = b->parity;
+        if (b->reduced) c->m_valid = 1;
+    }
     return LB_OK;
+}
+
+int lb_batch_set_form(lb_batch *b, int reduced)
+{
+    if (!b || (reduced != 0 && reduced != 1)) return LB_ERR_INVALID;
+    if (reduced == b->reduced) return LB_OK;
+    if (reduced)
+        for (lb_ctx *c : b->ctx)
+            if (c->p.tau_g != 1.0) return LB_ERR_INVALID;
+    int rc = batch_sync(b);
+    for (lb_ctx *c : b->ctx) {
+        if (!rc) rc = lbk::taug1_convert(c, reduced);
+        if (!rc) c->reduced = reduced;
+    }
+    if (!rc) rc = lbk::cuda_status(cudaStreamSynchronize(b->user_stream));
+    if (rc) return rc;
+    b->reduced = reduced;
+    return tables(b);
 }
 
 int lb_batch_sync(lb_batch *b)

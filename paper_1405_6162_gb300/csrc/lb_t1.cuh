@@ -1,0 +1,250 @@
+// lb_t1.cuh -- per-site and per-tile pieces of the tau_g = 1 reduced form,
+// shared by the one-lattice kernels (lb_taug1.cu) and the ensemble kernel
+// (lb_batch.cu).  The storage and the two passes are described in
+// lb_taug1.cu.
+#pragma once
+
+#include "d3q19.cuh"
+#include "lb_site.cuh"
+
+namespace lbk {
+
+// a source site's moments expanded for geq: base by c^2 (0, 1, 2), 3 phi, 9/2 phi, u
+template <typename T>
+struct Eq {
+    T b0, b1, b2, a3, a45, ux, uy, uz;
+};
+
+template <typename T>
+__device__ __forceinline__ Eq<T> make_eq(T phi, T gmh, T ux, T uy, T uz)
+{
+    Eq<T> e;
+    const T u2 = ux * ux + uy * uy + uz * uz;
+    e.b1 = phi - T(1.5) * phi * u2;
+    e.b0 = e.b1 - gmh;
+    e.b2 = e.b1 + gmh;
+    e.a3 = T(3) * phi;
+    e.a45 = T(4.5) * phi;
+    e.ux = ux;
+    e.uy = uy;
+    e.uz = uz;
+    return e;
+}
+
+template <typename T>
+__device__ __forceinline__ T gmh_of(T phi, T mu, T gamma)
+{
+    return T(4.5) * (gamma * mu - phi * T(1.0 / 3.0));
+}
+
+// c_i . u with the zero components left out; i a literal after inlining
+template <typename T>
+__device__ __forceinline__ T cdot(int i, T ux, T uy, T uz)
+{
+    T r = cx(i) > 0 ? ux : -ux;
+    if (cx(i) == 0) r = cy(i) > 0 ? uy : -uy;
+    else if (cy(i) != 0) r = cy(i) > 0 ? r + uy : r - uy;
+    if (cx(i) == 0 && cy(i) == 0) r = cz(i) > 0 ? uz : -uz;
+    else if (cz(i) != 0) r = cz(i) > 0 ? r + uz : r - uz;
+    return r;
+}
+
+// geq_i from expanded moments; i a literal after inlining
+template <typename T>
+__device__ __forceinline__ T geq_eq(int i, const Eq<T> &e)
+{
+    const int c2 = cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i);
+    if (c2 == 0) {
+        if constexpr (sizeof(T) == 4) {
+            // the float weights sum to 1 + e1 and their (c^2 - 1) moment is e2
+            // instead of 0 (e1, e2 from the rounded values); the rest term
+            // removes the bias e1 P + e2 gmh they would give sum_i geq_i
+            constexpr double w0f = double(float(1.0 / 3.0)), w1f = double(float(1.0 / 18.0)),
+                             w2f = double(float(1.0 / 36.0));
+            constexpr float e1 = float(w0f + 6.0 * w1f + 12.0 * w2f - 1.0);
+            constexpr float e2 = float(12.0 * w2f - w0f);
+            return T(weight(0)) * e.b0 - (e1 * e.b1 + e2 * (e.b1 - e.b0));
+        }
+        return T(weight(0)) * e.b0;
+    }
+    const T cu = cdot(i, e.ux, e.uy, e.uz);
+    const T base = c2 == 1 ? e.b1 : e.b2;
+    return T(weight(i)) * (base + cu * (e.a3 + e.a45 * cu));
+}
+
+// the quad (gmh, u) of a site: one vector access
+template <typename T>
+struct Quad;
+template <>
+struct Quad<float> {
+    static __device__ __forceinline__ void load(const float *__restrict__ q, long long s, float (&v)[4])
+    {
+        const float4 a = reinterpret_cast<const float4 *>(q)[s];
+        v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+    }
+    static __device__ __forceinline__ void store(float *__restrict__ q, long long s, float a, float b, float c,
+                                                 float d)
+    {
+        reinterpret_cast<float4 *>(q)[s] = make_float4(a, b, c, d);
+    }
+};
+template <>
+struct Quad<double> {
+    static __device__ __forceinline__ void load(const double *__restrict__ q, long long s, double (&v)[4])
+    {
+        const double2 a = reinterpret_cast<const double2 *>(q)[2 * s], b = reinterpret_cast<const double2 *>(q)[2 * s + 1];
+        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+    }
+    static __device__ __forceinline__ void store(double *__restrict__ q, long long s, double a, double b, double c,
+                                                 double d)
+    {
+        reinterpret_cast<double2 *>(q)[2 * s] = make_double2(a, b);
+        reinterpret_cast<double2 *>(q)[2 * s + 1] = make_double2(c, d);
+    }
+};
+
+// the quads start at component 1 (S is a multiple of 64 elements, so they are aligned)
+template <typename T>
+__device__ __forceinline__ const T *quads(const T *g, long long S) { return g + S; }
+template <typename T>
+__device__ __forceinline__ T *quads(T *g, long long S) { return g + S; }
+
+// moments of site src stored in the reduced form
+template <typename T>
+__device__ __forceinline__ Eq<T> load_eq(const T *__restrict__ g, long long S, long long src)
+{
+    T v[4];
+    Quad<T>::load(quads(g, S), src, v);
+    return make_eq(g[src], v[0], v[1], v[2], v[3]);
+}
+
+// The collide pass at site s: pull f, the NP-point stencil of phi(t) from
+// component 0 of level a, the general collision's f part; write f* and the
+// quad (gmh, u) of (s, t) into level a.
+template <typename T, bool SH, int NP>
+__device__ __forceinline__ void t1_collide_site(const T *__restrict__ fa, T *__restrict__ ga, T *__restrict__ fb,
+                                                const Coll<T> &p, int nx, int ny, int nz, long long S, int s)
+{
+    const Nbr n(s, nx, ny, nz);
+    const T *phi = ga;
+    T f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) f[i] = fa[(size_t)i * S + n.src(i)];
+    const T ph = phi[s];
+    T dx, dy, dz, lap;
+    stencil_np<NP, T>(phi, n, ph, dx, dy, dz, lap);
+    // the general collision's f part; g's result is its equilibrium, kept as moments
+    T ux, uy, uz, mu;
+    collide_f<T, SH>(p, f, ph, dx, dy, dz, lap, ux, uy, uz, mu);
+#pragma unroll
+    for (int i = 0; i < Q; i++) fb[(size_t)i * S + s] = f[i];
+    Quad<T>::store(quads(ga, S), s, gmh_of(ph, mu, p.gamma), ux, uy, uz);
+}
+
+constexpr int kPhiOut = 30;    // output columns per warp
+
+#ifndef LBK_T1_KY32
+#define LBK_T1_KY32 1
+#endif
+#ifndef LBK_T1_KY64
+#define LBK_T1_KY64 2
+#endif
+template <typename T>
+struct PhiTile {
+    static constexpr int KY = sizeof(T) == 8 ? LBK_T1_KY64 : LBK_T1_KY32;   // y rows per lane
+};
+
+__device__ __forceinline__ int wrap_up(int v, int n)
+{
+    while (v >= n) v -= n;   // v < 2n + 32: a few iterations at most
+    return v;
+}
+
+// The phi pass for the tile of one warp: x columns bx*30 - 1 .. bx*30 + 30
+// (lane = column - bx*30 + 1), y rows y0 .. y0 + KY - 1, output planes
+// bz*kzc .. bz*kzc + kzc - 1.  No block-level synchronisation.
+template <typename T, int KY>
+__device__ __forceinline__ void t1_phi_tile(const T *__restrict__ ga, T *__restrict__ gb, int nx, int ny, int nz,
+                                            int kzc, long long S, int bx, int y0, int bz, int lane)
+{
+    if (y0 >= ny) return;   // uniform over the warp
+    const int z0 = bz * kzc;
+    const int nzc = min(kzc, nz - z0);   // output planes z0 .. z0 + nzc - 1
+    const int xu = bx * kPhiOut + lane - 1;   // unwrapped column, -1 .. nx + 30
+    const int x = wrap_up(xu + nx, nx);
+    const bool out_x = lane >= 1 && lane <= kPhiOut && xu < nx;
+    const long long plane = (long long)nx * ny;
+    int yoff[KY + 2];
+#pragma unroll
+    for (int k = 0; k < KY + 2; k++) yoff[k] = wrap_up(y0 - 1 + k + ny, ny) * nx;
+    // partial sums of output plane oz live in slot oz mod 3
+    T acc[3][KY], acc_r[3][KY], acc_l[3][KY];
+#pragma unroll
+    for (int q = 0; q < 3; q++)
+#pragma unroll
+        for (int a = 0; a < KY; a++) acc[q][a] = acc_r[q][a] = acc_l[q][a] = T(0);
+    // raw moments of the next source plane, loaded one plane ahead
+    int zr = wrap_up(z0 - 1 + nz, nz);   // source plane of step j: z0 + j - 1
+    const T *q0 = quads(ga, S);
+    T nxt[KY + 2][5];
+#pragma unroll
+    for (int r = 0; r < KY + 2; r++) {
+        const long long o = x + zr * plane + yoff[r];
+        T v[4];
+        Quad<T>::load(q0, o, v);
+        nxt[r][0] = ga[o], nxt[r][1] = v[0], nxt[r][2] = v[1], nxt[r][3] = v[2], nxt[r][4] = v[3];
+    }
+    for (int j0 = 0; j0 < nzc + 2; j0 += 3) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const int j = j0 + k;
+            if (j >= nzc + 2) break;   // uniform over the warp
+            T cur[KY + 2][5];
+#pragma unroll
+            for (int r = 0; r < KY + 2; r++)
+#pragma unroll
+                for (int m = 0; m < 5; m++) cur[r][m] = nxt[r][m];
+            zr = zr + 1 == nz ? 0 : zr + 1;
+            const long long zo = zr * plane;   // one plane past the last is still in range
+#pragma unroll
+            for (int r = 0; r < KY + 2; r++) {
+                const long long o = x + zo + yoff[r];
+                T v[4];
+                Quad<T>::load(q0, o, v);
+                nxt[r][0] = ga[o], nxt[r][1] = v[0], nxt[r][2] = v[1], nxt[r][3] = v[2], nxt[r][4] = v[3];
+            }
+#pragma unroll
+            for (int ry = -1; ry <= KY; ry++) {
+                const T *c5 = cur[ry + 1];
+                const Eq<T> e = make_eq(c5[0], c5[1], c5[2], c5[3], c5[4]);
+#pragma unroll
+                for (int i = 0; i < Q; i++) {
+                    const int oy = ry + cy(i);
+                    if (oy < 0 || oy >= KY) continue;
+                    const int q = (k + 2 + cz(i)) % 3;   // slot of output plane j - 1 + c_z
+                    const T v = geq_eq(i, e);
+                    if (cx(i) == 0)
+                        acc[q][oy] += v;
+                    else if (cx(i) > 0)
+                        acc_r[q][oy] += v;   // to column x + 1
+                    else
+                        acc_l[q][oy] += v;   // to column x - 1
+                }
+            }
+            // output plane j - 2 (slot (k + 1) mod 3) is complete
+            const int qd = (k + 1) % 3;
+            const int oz = j - 2;
+#pragma unroll
+            for (int a = 0; a < KY; a++) {
+                const T from_left = __shfl_up_sync(0xffffffffu, acc_r[qd][a], 1);
+                const T from_right = __shfl_down_sync(0xffffffffu, acc_l[qd][a], 1);
+                if (out_x && oz >= 0 && y0 + a < ny)
+                    gb[x + yoff[a + 1] + (z0 + oz) * plane] = acc[qd][a] + (from_left + from_right);
+                acc[qd][a] = acc_r[qd][a] = acc_l[qd][a] = T(0);
+            }
+        }
+    }
+}
+
+
+}  // namespace lbk
