@@ -228,6 +228,11 @@ def _ensemble(torch):
         # every lattice has tau_g = 1: the same ensemble in the reduced form
         b.set_form("taug1")
         init(b)
+        cfg1 = tuning.batch_config(b)
+        if cfg1 is None:
+            cfg1, _ = tuning.autotune_batch(b, steps=10)
+            init(b)
+        b.set_launch(*cfg1)
         b.run(500)
         b.sync()
         init(b)
@@ -237,7 +242,9 @@ def _ensemble(torch):
         e.synchronize()
         b.sync()
         t1 = s.elapsed_time(e) / 1e3
+        info1 = b.info()
         out["taug1"] = {"seconds": t1, "MLUPS": b.sites * 500 / t1 / 1e6,
+                        "launch": {"threads": info1[3], "ctas": info1[2], "work_items": info1[1]},
                         "hbm_frac": b.sites * 500 * BYTES_PER_SITE_TAUG1["fp32_shifted"] / t1 / 1e9 / _peaks()[0],
                         "what": "lb_batch_set_form(taug1): the tau_g = 1 reduced form for every lattice"}
         return out

@@ -35,6 +35,7 @@ class Batch:
         sp = self.stream.cuda_stream if hasattr(self.stream, "cuda_stream") else int(self.stream)
         self.specs = [dict(d) for d in lattices]
         self.precision = precision
+        self.form = "general"
         arr = (L.lb_params * len(self.specs))()
         for k, d in enumerate(self.specs):
             arr[k] = L.lb_params(d["nx"], d["ny"], d["nz"], d["tau"], d["tau_g"], d["rho0"], d["gamma"],
@@ -76,6 +77,7 @@ class Batch:
     def set_form(self, form: str = "general"):
         """"general" two-pass step or the tau_g = 1 "taug1" reduced form."""
         L.check(L.lib().lb_batch_set_form(self.handle, {"general": 0, "taug1": 1}[form]), "lb_batch_set_form")
+        self.form = form
 
     def set_launch(self, threads: int = 256, ctas_per_sm: int = 0):
         L.check(L.lib().lb_batch_set_launch(self.handle, int(threads), int(ctas_per_sm)), "lb_batch_set_launch")

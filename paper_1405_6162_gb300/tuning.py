@@ -102,7 +102,7 @@ def autotune(dims, precision, params, phi0, configs=None, steps=5, save=True, lo
 def _batch_key(batch) -> str:
     import hashlib
     h = hashlib.sha256(repr([sorted(d.items()) for d in batch.specs]).encode()).hexdigest()[:12]
-    return f"{_gpu_name()}|batch{len(batch)}:{h}|{batch.precision}"
+    return f"{_gpu_name()}|batch{len(batch)}:{h}|{batch.precision}|{getattr(batch, 'form', 'general')}"
 
 
 def batch_candidates(precision):
