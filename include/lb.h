@@ -69,9 +69,9 @@ enum {
     LB_FP64_DF = 2        /* double-float: each value stored and computed as
                              an unevaluated sum of two floats (~48 bits,
                              unit roundoff ~2^-48), on the FP32 units; the
-                             default two-pass step only (LB_KERNEL_AUTO /
-                             LB_KERNEL_TWO_PASS), not in ensembles or the
-                             adjoint                                         */
+                             default two-pass step and the tau_g = 1 reduced
+                             form only (LB_KERNEL_AUTO / _TWO_PASS / _TAUG1),
+                             not in ensembles or the adjoint                 */
 };
 
 enum { LB_HOST = 0, LB_DEVICE = 1 };

@@ -382,7 +382,8 @@ int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk)
     if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_TAUG1 || c->batch_owned) return LB_ERR_INVALID;
     if (block_x < 0 || block_y < 0 || z_chunk < 0) return LB_ERR_INVALID;
     if (c->npts != 7 && seven_point_only(kernel)) return LB_ERR_INVALID;
-    if (c->p.precision == LB_FP64_DF && kernel != LB_KERNEL_AUTO && kernel != LB_KERNEL_TWO_PASS)
+    if (c->p.precision == LB_FP64_DF && kernel != LB_KERNEL_AUTO && kernel != LB_KERNEL_TWO_PASS &&
+        kernel != LB_KERNEL_TAUG1)
         return LB_ERR_INVALID;
     if (lbk::uses_mrt(c) && kernel != LB_KERNEL_AUTO && kernel != LB_KERNEL_TWO_PASS) return LB_ERR_INVALID;
     if (kernel == LB_KERNEL_STAGED) {

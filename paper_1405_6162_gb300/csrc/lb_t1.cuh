@@ -5,6 +5,7 @@
 #pragma once
 
 #include "d3q19.cuh"
+#include "df64.cuh"
 #include "lb_site.cuh"
 
 namespace lbk {
@@ -103,6 +104,42 @@ struct Quad<double> {
     }
 };
 
+template <>
+struct Quad<df64> {
+    static __device__ __forceinline__ void load(const df64 *__restrict__ q, long long s, df64 (&v)[4])
+    {
+        const float4 a = reinterpret_cast<const float4 *>(q)[2 * s], b = reinterpret_cast<const float4 *>(q)[2 * s + 1];
+        v[0] = df64(a.x, a.y), v[1] = df64(a.z, a.w), v[2] = df64(b.x, b.y), v[3] = df64(b.z, b.w);
+    }
+    static __device__ __forceinline__ void store(df64 *__restrict__ q, long long s, df64 a, df64 b, df64 c, df64 d)
+    {
+        reinterpret_cast<float4 *>(q)[2 * s] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        reinterpret_cast<float4 *>(q)[2 * s + 1] = make_float4(c.hi, c.lo, d.hi, d.lo);
+    }
+};
+
+// warp shuffles of one value (a double-float moves as its two floats)
+template <typename T>
+__device__ __forceinline__ T shfl_up1(T v)
+{
+    return __shfl_up_sync(0xffffffffu, v, 1);
+}
+template <typename T>
+__device__ __forceinline__ T shfl_down1(T v)
+{
+    return __shfl_down_sync(0xffffffffu, v, 1);
+}
+template <>
+__device__ __forceinline__ df64 shfl_up1(df64 v)
+{
+    return df64(__shfl_up_sync(0xffffffffu, v.hi, 1), __shfl_up_sync(0xffffffffu, v.lo, 1));
+}
+template <>
+__device__ __forceinline__ df64 shfl_down1(df64 v)
+{
+    return df64(__shfl_down_sync(0xffffffffu, v.hi, 1), __shfl_down_sync(0xffffffffu, v.lo, 1));
+}
+
 // the quads start at component 1 (S is a multiple of 64 elements, so they are aligned)
 template <typename T>
 __device__ __forceinline__ const T *quads(const T *g, long long S) { return g + S; }
@@ -149,9 +186,13 @@ constexpr int kPhiOut = 30;    // output columns per warp
 #ifndef LBK_T1_KY64
 #define LBK_T1_KY64 2
 #endif
+#ifndef LBK_T1_KYDF
+#define LBK_T1_KYDF 2
+#endif
 template <typename T>
 struct PhiTile {
-    static constexpr int KY = sizeof(T) == 8 ? LBK_T1_KY64 : LBK_T1_KY32;   // y rows per lane
+    // y rows per lane
+    static constexpr int KY = is_df64<T>::value ? LBK_T1_KYDF : sizeof(T) == 8 ? LBK_T1_KY64 : LBK_T1_KY32;
 };
 
 __device__ __forceinline__ int wrap_up(int v, int n)
@@ -236,8 +277,8 @@ __device__ __forceinline__ void t1_phi_tile(const T *__restrict__ ga, T *__restr
             const int oz = j - 2;
 #pragma unroll
             for (int a = 0; a < KY; a++) {
-                const T from_left = __shfl_up_sync(0xffffffffu, acc_r[qd][a], 1);
-                const T from_right = __shfl_down_sync(0xffffffffu, acc_l[qd][a], 1);
+                const T from_left = shfl_up1(acc_r[qd][a]);
+                const T from_right = shfl_down1(acc_l[qd][a]);
                 if (out_x && oz >= 0 && y0 + a < ny)
                     gb[x + yoff[a + 1] + (z0 + oz) * plane] = acc[qd][a] + (from_left + from_right);
                 acc[qd][a] = acc_r[qd][a] = acc_l[qd][a] = T(0);

@@ -254,7 +254,7 @@ void g_rows_t(lb_ctx *c, int i0, int i1, double *out)
 
 int launch_step_taug1(lb_ctx *c, int nsteps)
 {
-    return c->p.precision == LB_FP64 ? run_t1_t<double, false>(c, nsteps) : run_t1_t<float, true>(c, nsteps);
+    return by_precision(c, [&](auto P) { return run_t1_t<typename decltype(P)::T, decltype(P)::SH>(c, nsteps); });
 }
 
 // convert the stored state between the full and the reduced form
@@ -263,30 +263,22 @@ int taug1_convert(lb_ctx *c, int to_reduced)
     const int cur = c->buf.cur;
     const unsigned grid = grid_of(c->N);
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
-    if (to_reduced) {
-        // phi(t) into the phi scratch, then into component 0 of level cur
-        if (c->p.precision == LB_FP64) {
-            k_t1_from_full<double><<<grid, kT1Threads, 0, c->stream>>>((const double *)c->buf.g[cur], (double *)c->phi,
-                                                                       nx, ny, nz, c->S);
-            k_t1_copy_phi<double><<<grid, kT1Threads, 0, c->stream>>>((const double *)c->phi,
-                                                                      (double *)c->buf.g[cur], c->N);
+    return by_precision(c, [&](auto P) {
+        using T = typename decltype(P)::T;
+        if (to_reduced) {
+            // phi(t) into the phi scratch, then into component 0 of level cur
+            k_t1_from_full<T><<<grid, kT1Threads, 0, c->stream>>>((const T *)c->buf.g[cur], (T *)c->phi, nx, ny, nz,
+                                                                  c->S);
+            k_t1_copy_phi<T><<<grid, kT1Threads, 0, c->stream>>>((const T *)c->phi, (T *)c->buf.g[cur], c->N);
+            c->m_valid = 0;
         } else {
-            k_t1_from_full<float><<<grid, kT1Threads, 0, c->stream>>>((const float *)c->buf.g[cur], (float *)c->phi,
-                                                                      nx, ny, nz, c->S);
-            k_t1_copy_phi<float><<<grid, kT1Threads, 0, c->stream>>>((const float *)c->phi, (float *)c->buf.g[cur],
-                                                                     c->N);
+            // back to the full form: phi(t) into the phi scratch, then the 19
+            // values of g rebuilt into the current level (the previous step's
+            // moments are read from the other level)
+            to_full_t<T, decltype(P)::SH>(c);
         }
-        c->m_valid = 0;
         return check_launch();
-    }
-    // back to the full form: phi(t) into the phi scratch, then the 19 values
-    // of g rebuilt into the current level (the previous step's moments are
-    // read from the other level)
-    if (c->p.precision == LB_FP64)
-        to_full_t<double, false>(c);
-    else
-        to_full_t<float, true>(c);
-    return check_launch();
+    });
 }
 
 template <typename T>
@@ -301,20 +293,19 @@ int taug1_phi_out(lb_ctx *c, double *out)
 {
     const unsigned grid = grid_of(c->N);
     const int cur = c->buf.cur;
-    if (c->p.precision == LB_FP64)
-        k_t1_phi_out<double><<<grid, kT1Threads, 0, c->stream>>>((const double *)c->buf.g[cur], out, c->N);
-    else
-        k_t1_phi_out<float><<<grid, kT1Threads, 0, c->stream>>>((const float *)c->buf.g[cur], out, c->N);
-    return check_launch();
+    return by_precision(c, [&](auto P) {
+        using T = typename decltype(P)::T;
+        k_t1_phi_out<T><<<grid, kT1Threads, 0, c->stream>>>((const T *)c->buf.g[cur], out, c->N);
+        return check_launch();
+    });
 }
 
 int taug1_g_rows(lb_ctx *c, int i0, int i1, double *out)
 {
-    if (c->p.precision == LB_FP64)
-        g_rows_t<double, false>(c, i0, i1, out);
-    else
-        g_rows_t<float, true>(c, i0, i1, out);
-    return check_launch();
+    return by_precision(c, [&](auto P) {
+        g_rows_t<typename decltype(P)::T, decltype(P)::SH>(c, i0, i1, out);
+        return check_launch();
+    });
 }
 
 }  // namespace lbk

@@ -80,28 +80,44 @@ def test_stencil_and_mrt_match_oracle():
     assert rel(to_oracle(f), fo) <= TOL_FP64 and rel(to_oracle(g), go) <= TOL_FP64
 
 
-def test_spinodal_64cubed_1000_steps():
+@pytest.mark.parametrize("kernel", ["auto", "taug1"])
+def test_spinodal_64cubed_1000_steps(kernel):
     dims = (64, 64, 64)
     phi0 = L.spinodal_phi0(*dims, seed=1)
     fo, go = oracle.step(dims, P0, *oracle.init(dims, P0, phi0), 1000, kind="omp")
     want = oracle.moments(dims, fo, go)
     with _lat(dims) as lat:
+        lat.set_kernel(kernel)
         lat.init(phi0)
         lat.step(1000)
         got = lat.moments()
     errs = {k: rel(a, b, u_scale(fo) if k == "u" else None) for k, a, b in zip(("rho", "u", "phi"), got, want)}
-    print("spinodal 64^3 x 1000 fp64_df:", errs)
+    print(f"spinodal 64^3 x 1000 fp64_df {kernel}:", errs)
     for k, e in errs.items():
         assert e <= 1e-11, (k, e)
+
+
+@pytest.mark.parametrize("dims", [(32, 32, 32), (13, 7, 5), (70, 37, 11), (1, 1, 9)])
+def test_reduced_form_matches_oracle(dims):
+    phi0 = L.spinodal_phi0(*dims, seed=1030, amp=0.4)
+    fo, go = oracle.step(dims, P0, *oracle.init(dims, P0, phi0), 10)
+    with _lat(dims) as lat:
+        lat.set_kernel("taug1")
+        lat.init(phi0)
+        lat.step(10)
+        _check(lat.moments(), oracle.moments(dims, fo, go), TOL_FP64, fo)
+        f, g = lat.get_state()
+    assert rel(to_oracle(f), fo) <= TOL_FP64 and rel(to_oracle(g), go) <= TOL_FP64
 
 
 def test_limits():
     from paper_1405_6162_gb300 import Batch, LBError
     dims = (8, 6, 5)
     with _lat(dims) as lat:
-        for k in ("fused", "staged", "slab", "lag", "taug1"):
+        for k in ("fused", "staged", "slab", "lag"):
             with pytest.raises(LBError):
                 lat.set_kernel(k)
+        lat.set_kernel("taug1")
         lat.set_kernel("two_pass")
     with pytest.raises(LBError):
         Batch([dict(P0, nx=8, ny=6, nz=5)], precision="fp64_df")
