@@ -59,6 +59,16 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(v, ws, device="cuda"):
+    """The maximum of v over the ranks (the job's time is its slowest rank's)."""
+    if ws == 1:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -307,13 +317,6 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(v):
-        if ws == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-
     results = {}
     for prec in ("fp32_shifted", "fp64"):
         cfg = tuning.bench_config(DIMS, prec)
@@ -329,7 +332,7 @@ def run_ours(args):
                 lat.step(args.steps)
                 stop.record()
                 barrier()
-            wall = max_over_ranks(start.elapsed_time(stop) / 1e3)
+            wall = max_over_ranks(start.elapsed_time(stop) / 1e3, ws)
             # per-launch durations of the same kernel for the roofline
             per = _time_steps(lat, max(5, min(args.steps, 20)), torch)
             r = lat.reduce()
@@ -356,7 +359,7 @@ def run_ours(args):
                 lat.step(k)
                 stop.record()
                 barrier()
-            wall = max_over_ranks(start.elapsed_time(stop) / 1e3)
+            wall = max_over_ranks(start.elapsed_time(stop) / 1e3, ws)
             per = _time_steps(lat, max(5, min(k, 20)), torch)
         return dict(wall=wall, steps=k, t_launch=float(np.mean(per)), clocks=clk.summary())
 
@@ -425,7 +428,7 @@ def run_ours(args):
             rc = lib.lb_moments(lbl, None, None, out_host.ctypes.data, 0)   # D2H of the result
             assert rc == 0
         barrier()
-        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        t_e2e = max_over_ranks(time.perf_counter() - t0, ws)
     e2e = {"value": ws * n * E2E_STEPS * e2e_iters / t_e2e / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": n * 8 / E2E_STEPS, "d2h_bytes_per_step": n * 8 / E2E_STEPS,
            "steps_per_transfer": E2E_STEPS}
