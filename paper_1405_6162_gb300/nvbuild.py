@@ -44,8 +44,19 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "lb.h")]
 
 
+def _manifest() -> str:
+    """The set of dependency files (a removed or added file forces a rebuild)."""
+    return "\n".join(os.path.basename(d) for d in sorted(_deps())) + "\n"
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
+        return False
+    try:
+        with open(os.path.join(OUT_DIR, "manifest.txt")) as fh:
+            if fh.read() != _manifest():
+                return False
+    except OSError:
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(d) <= t for d in _deps())
@@ -83,6 +94,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), out_dir=No
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, lib_path)
+    with open(os.path.join(OUT, "manifest.txt"), "w") as fh:
+        fh.write(_manifest())
     if verbose:
         print(open(os.path.join(OUT, "ptxas.log")).read())
     return lib_path
