@@ -457,8 +457,12 @@ def run_ours(args):
             fl = _profile_value(prof, "fp64_flops_per_site")
             pk = _profile_value(prof, "fp64_peak_tflops", need_current=False)
             achieved = fl * n / r["t_launch"] / 1e12 if fl else None
+            ins = _profile_value(prof, "fp64_instr_per_site")
             roof = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
                     "frac": (achieved / pk) if (achieved and pk) else None,
+                    # FP64 adds and multiplies occupy the pipe like an FMA: the
+                    # instruction rate against the FMA-instruction peak (peak / 2)
+                    "pipe_frac": (ins * n / r["t_launch"] / (pk * 1e12 / 2)) if (ins and pk) else None,
                     "traffic": _profile_value(prof, "dram_bytes_per_step"),
                     "peak_kind": "measured FP64 FMA throughput (profiles/step_fp64_256cubed.md)",
                     "hbm_frac": BYTES_PER_SITE[prec] * n / r["t_launch"] / 1e9 / peak}
