@@ -138,8 +138,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kBatchMaxThreads64 : kBatchMa
             }
             if (!grid_sync(bar, gridDim.x, timeout_ns, err, &s_fail)) return;
         }
-        return;
-    }
+    } else {
     for (int t = 0; t < nsteps; t++) {
         const int a = (parity0 + t) & 1;
         for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
@@ -164,6 +163,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kBatchMaxThreads64 : kBatchMa
             }
         }
         if (!grid_sync(bar, gridDim.x, timeout_ns, err, &s_fail)) return;
+    }
     }
 }
 

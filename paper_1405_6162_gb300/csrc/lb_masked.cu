@@ -2,11 +2,11 @@
 // sites whose mask byte is non-zero, in site order (targetDP Sec. III.B,
 // copyFromTargetMasked / copyToTargetMasked).
 //
-// A stream compaction: per-CTA counts of selected sites (one site per thread,
-// __syncthreads_count), one CTA's exclusive scan of the counts (offsets[nb] =
-// total), then the list of selected sites, each thread placing its site by
-// the CTA offset, the warp prefix of the warps before it and a ballot within
-// its warp.  The gather / scatter kernels then run one thread per selected
+// A stream compaction: per-CTA counts of selected sites (16 mask bytes per
+// thread, one vector load when aligned), one CTA's exclusive scan of the
+// counts (offsets[nb] = total), then the list of selected sites, each thread
+// placing its 16 sites after the CTA offset and the counts of the threads
+// before it (a block scan).  The gather / scatter kernels then run one thread per selected
 // site, so every thread has work whatever the mask's density.  The order is
 // the site order, so the result is unique and bit-exact.
 #include <cuda_runtime.h>
@@ -19,17 +19,54 @@ namespace lbk {
 
 namespace {
 
-constexpr int kMaskThreads = 512;               // sites per CTA, one per thread
+constexpr int kMaskThreads = 512;               // threads of the one-CTA scan
 constexpr int kMaskWarps = kMaskThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
 static_assert(kMaskThreads % 32 == 0 && kMaskWarps <= 32, "CTA of whole warps, at most 32");
 
-__global__ void __launch_bounds__(kMaskThreads) k_mask_count(const unsigned char *__restrict__ mask, long long N,
+constexpr int kTileThreads = 256;                 // compaction CTAs
+constexpr int kPerThread = 16;                    // mask bytes per thread
+constexpr int kTile = kTileThreads * kPerThread;  // sites per compaction CTA
+
+// the 16 mask bytes of a thread as non-zero flags (bit k = site base + k);
+// one 16-byte load when the chunk is aligned and inside the mask
+template <bool VEC>
+__device__ __forceinline__ unsigned mask_bits(const unsigned char *__restrict__ mask, long long base, long long N)
+{
+    unsigned bits = 0;
+    if (VEC && base + kPerThread <= N) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(mask + base);
+        const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if ((w[q] >> (8 * k)) & 0xffu) bits |= 1u << (4 * q + k);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kPerThread; k++)
+            if (base + k < N && mask[base + k] != 0) bits |= 1u << k;
+    }
+    return bits;
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(kTileThreads) k_mask_count(const unsigned char *__restrict__ mask, long long N,
                                                              int *__restrict__ counts)
 {
-    const long long s = (long long)blockIdx.x * kMaskThreads + threadIdx.x;
-    const int c = __syncthreads_count(s < N && mask[s] != 0);
-    if (threadIdx.x == 0) counts[blockIdx.x] = c;
+    __shared__ int warp_cnt[kTileThreads / 32];
+    const long long base = (long long)blockIdx.x * kTile + (long long)threadIdx.x * kPerThread;
+    int c = __popc(mask_bits<VEC>(mask, base, N));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) warp_cnt[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+#pragma unroll
+        for (int w = 0; w < kTileThreads / 32; w++) t += warp_cnt[w];
+        counts[blockIdx.x] = t;
+    }
 }
 
 // inclusive scan over a warp
@@ -73,33 +110,26 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask_scan(const int *__restric
     if (threadIdx.x == 0) offsets[nb] = carry_s;
 }
 
-// compact index of this thread's site among the selected ones (all threads
-// of the CTA must call it)
-__device__ __forceinline__ int compact_index(bool flag, const int *__restrict__ offsets)
-{
-    __shared__ int warp_pre[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned bal = __ballot_sync(kFull, flag);
-    const int before = __popc(bal & ((1u << lane) - 1u));
-    if (lane == 0) warp_pre[warp] = __popc(bal);
-    __syncthreads();
-    if (warp == 0) {
-        const int v = lane < kMaskWarps ? warp_pre[lane] : 0;
-        const int t = warp_incl(v) - v;
-        if (lane < kMaskWarps) warp_pre[lane] = t;
-    }
-    __syncthreads();
-    return offsets[blockIdx.x] + warp_pre[warp] + before;
-}
-
-// idx[k] = site of the k-th selected site (site order)
-__global__ void __launch_bounds__(kMaskThreads) k_mask_index(const unsigned char *__restrict__ mask, long long N,
+// idx[k] = site of the k-th selected site (site order): each thread's 16
+// sites are placed after the selected sites of the CTAs before it (offsets)
+// and of the threads before it in its CTA (a block scan of the counts)
+template <bool VEC>
+__global__ void __launch_bounds__(kTileThreads) k_mask_index(const unsigned char *__restrict__ mask, long long N,
                                                              const int *__restrict__ offsets, int *__restrict__ idx)
 {
-    const long long s = (long long)blockIdx.x * kMaskThreads + threadIdx.x;
-    const bool flag = s < N && mask[s] != 0;
-    const int dst = compact_index(flag, offsets);
-    if (flag) idx[dst] = (int)s;
+    __shared__ int warp_tot[kTileThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long base = (long long)blockIdx.x * kTile + (long long)threadIdx.x * kPerThread;
+    const unsigned bits = mask_bits<VEC>(mask, base, N);
+    const int c = __popc(bits);
+    const int incl = warp_incl(c);
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    int before = offsets[blockIdx.x] + incl - c;
+    for (int w = 0; w < warp; w++) before += warp_tot[w];
+#pragma unroll
+    for (int k = 0; k < kPerThread; k++)
+        if (bits & (1u << k)) idx[before++] = (int)(base + k);
 }
 
 constexpr int kGatherThreads = 256;   // one selected site per thread
@@ -176,7 +206,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_masked_set(T *__restrict__ a
     }
 }
 
-inline int mask_blocks(long long N) { return (int)((N + kMaskThreads - 1) / kMaskThreads); }
+inline int mask_blocks(long long N) { return (int)((N + kTile - 1) / kTile); }
 
 inline unsigned gather_blocks(long long total) { return (unsigned)((total + kGatherThreads - 1) / kGatherThreads); }
 
@@ -190,9 +220,16 @@ int launch_mask_scan(lb_ctx *c, const unsigned char *mask_d, int *scratch)
 {
     const int nb = mask_blocks(c->N);
     int *counts = scratch, *offsets = scratch + nb, *idx = scratch + 2 * nb + 1;
-    k_mask_count<<<nb, kMaskThreads, 0, c->stream>>>(mask_d, c->N, counts);
+    const bool vec = ((unsigned long long)mask_d & 15) == 0;
+    if (vec)
+        k_mask_count<true><<<nb, kTileThreads, 0, c->stream>>>(mask_d, c->N, counts);
+    else
+        k_mask_count<false><<<nb, kTileThreads, 0, c->stream>>>(mask_d, c->N, counts);
     k_mask_scan<<<1, kMaskThreads, 0, c->stream>>>(counts, nb, offsets);
-    k_mask_index<<<nb, kMaskThreads, 0, c->stream>>>(mask_d, c->N, offsets, idx);
+    if (vec)
+        k_mask_index<true><<<nb, kTileThreads, 0, c->stream>>>(mask_d, c->N, offsets, idx);
+    else
+        k_mask_index<false><<<nb, kTileThreads, 0, c->stream>>>(mask_d, c->N, offsets, idx);
     return check_launch();
 }
 

@@ -166,3 +166,26 @@ def test_interface_band_at_256cubed(precision):
         assert (rho - P0["rho0"]).abs().max().item() <= tol * 2
         assert u.abs().max().item() <= tol
         assert np.abs(phi.cpu().numpy() - oracle.select_sites(phi0, m)).max() <= tol
+
+
+def test_unaligned_device_mask_and_ragged_tail():
+    """A device mask that does not start on a 16-byte boundary takes the
+    byte-wise path; a lattice whose size is not a multiple of the 4096-site
+    tile has a ragged last tile."""
+    import torch
+    dims = (17, 13, 11)
+    n = 2431
+    phi0 = L.spinodal_phi0(*dims, seed=960, amp=0.5)
+    m = (L.uniform(961, n, 0, 1) < 0.3).astype(np.uint8)
+    big = torch.zeros(n + 3, dtype=torch.uint8, device="cuda")
+    big[1:n + 1] = torch.from_numpy(m).cuda()
+    view = big[1:n + 1]
+    assert view.data_ptr() % 16 != 0
+    with _lat(dims) as lat:
+        lat.init(phi0)
+        lat.step(2)
+        full = lat.moments()
+        got = lat.moments_masked(view)
+        assert lat.count_masked(view) == int(m.sum())
+        for a, b in zip(got, full):
+            assert np.array_equal(a.cpu().numpy(), oracle.select_sites(b, m))
