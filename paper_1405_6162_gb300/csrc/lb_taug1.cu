@@ -33,6 +33,8 @@
 // each site (exact after lb_init, which starts from that equilibrium).
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "d3q19.cuh"
 #include "lb_internal.cuh"
 #include "lb_site.cuh"
@@ -168,14 +170,15 @@ int run_t1(lb_ctx *c, int nsteps)
     constexpr int KY = PhiTile<T>::KY;
     const unsigned gx = (nx + kPhiOut - 1) / kPhiOut, gy = (ny + KY * kPhiWarps - 1) / (KY * kPhiWarps);
     // z runs of 8..64 planes: as long as about three waves of resident blocks remain
-    static int per_sm[2] = {0, 0};
-    int &bps = per_sm[sizeof(T) == 8];
+    static std::atomic<int> bps_cache{0};   // per instantiation: resident phi-pass CTAs per SM
+    int bps = bps_cache.load(std::memory_order_relaxed);
     if (!bps) {
         int b = 0;
         const int rc1 = cuda_status(
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_t1_phi<T, KY>, 32 * kPhiWarps, 0));
         if (rc1) return rc1;
         bps = b > 0 ? b : 1;
+        bps_cache.store(bps, std::memory_order_relaxed);
     }
     int dev = 0, sms = 0;
     int rc0 = cuda_status(cudaGetDevice(&dev));
