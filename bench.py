@@ -201,9 +201,11 @@ def _oracle_errors(torch, params):
     return errs, base
 
 
-def _ensemble(torch):
+def _ensemble(torch, with_oracle=True):
     """The 64-lattice ensemble (sides U{16..64}, per-lattice tau and kappa,
-    FP32-shifted), 500 steps in one graph replay of one persistent launch."""
+    FP32-shifted), 500 steps in one graph replay of one persistent launch;
+    with_oracle: the reduced form's three smallest lattices against the
+    oracle after the 500 steps."""
     from paper_1405_6162_gb300 import Batch, tuning
     specs = LI.ensemble(3, 64)
 
@@ -253,7 +255,22 @@ def _ensemble(torch):
         b.sync()
         t1 = s.elapsed_time(e) / 1e3
         info1 = b.info()
-        out["taug1"] = {"seconds": t1, "MLUPS": b.sites * 500 / t1 / 1e6,
+        # per-lattice error of the three smallest lattices against the oracle
+        errs = []
+        if with_oracle:
+            import oracle
+            oracle.build()
+            small = sorted(range(len(specs)), key=lambda k: specs[k]["nx"] * specs[k]["ny"] * specs[k]["nz"])[:3]
+            for k in small:
+                d = specs[k]
+                dd = (d["nx"], d["ny"], d["nz"])
+                phi0k = LI.spinodal_phi0(*dd, seed=1000 + k)
+                fo, go = oracle.step(dd, d, *oracle.init(dd, d, phi0k), 500, kind="omp")
+                want = oracle.moments(dd, fo, go)
+                got = b[k].moments()
+                errs.append({"lattice": list(dd), **{nm: float(np.abs(a - w).max() / np.abs(w).max())
+                                                     for nm, a, w in zip(("rho", "u", "phi"), got, want)}})
+        out["taug1"] = {"seconds": t1, "MLUPS": b.sites * 500 / t1 / 1e6, "error_vs_oracle_500_steps": errs,
                         "launch": {"threads": info1[3], "ctas": info1[2], "work_items": info1[1]},
                         "hbm_frac": b.sites * 500 * BYTES_PER_SITE_TAUG1["fp32_shifted"] / t1 / 1e9 / _peaks()[0],
                         "what": "lb_batch_set_form(taug1): the tau_g = 1 reduced form for every lattice"}
@@ -292,9 +309,20 @@ def _adjoint(torch):
     kap = forward_backward()
     torch.cuda.synchronize()
     t_all = _t.perf_counter() - t0
+    # dJ/dkappa against central differences of the forward alone, Richardson
+    # extrapolated (J'' is large at these sizes, so plain O(h^2) differences
+    # at h = 1e-5 still differ at ~1e-5)
+    def loss(k):
+        with torch.no_grad():
+            return float(((trajectory(phi0, k, dims, params, T) - tgt) ** 2).sum().item())
+
+    k0 = params["kappa"]
+    fd = [(loss(k0 + h) - loss(k0 - h)) / (2 * h) for h in (2e-5, 1e-5)]
+    fd_rich = (4 * fd[1] - fd[0]) / 3
+    g = kap.grad.item()
     return {"lattice": list(dims), "steps": T, "precision": "fp64", "checkpoints": "every 14 steps (~sqrt T)",
             "forward_s": t_fwd, "forward_backward_s": t_all, "ratio": t_all / t_fwd,
-            "dJ_dkappa": kap.grad.item()}
+            "dJ_dkappa": g, "dJ_dkappa_fd_richardson": fd_rich, "rel_diff_vs_fd": abs(g - fd_rich) / abs(fd_rich)}
 
 
 def run_ours(args):
@@ -399,6 +427,24 @@ def run_ours(args):
     masked["achieved_gbs"] = masked["algorithmic_bytes"] / t_mask / 1e9
     masked["hbm_frac"] = masked["achieved_gbs"] / peak
 
+    # the 128^3 lattice of the 1000-step spinodal workload, both precisions
+    l128 = {}
+    for prec, k in (("fp32_shifted", 400), ("fp64", 50)):
+        d128 = (128, 128, 128)
+        with Lattice.from_params(d128, params, precision=prec) as lat:
+            lat.init(LI.spinodal_phi0(*d128, seed=1))
+            lat.step(args.warmup)
+            barrier()
+            start = torch.cuda.Event(enable_timing=True)
+            stop = torch.cuda.Event(enable_timing=True)
+            start.record()
+            lat.step(k)
+            stop.record()
+            barrier()
+            w = max_over_ranks(start.elapsed_time(stop) / 1e3, ws)
+        l128[prec] = {"MLUPS": ws * 128 ** 3 * k / w / 1e6, "steps": k,
+                      "l2": "state 0.6 / 1.3 GB, larger than L2"}
+
     # double-float (FP64-class accuracy on the FP32 units) on the default step
     df = timed("fp64_df", "auto", 7)
 
@@ -433,7 +479,7 @@ def run_ours(args):
            "h2d_bytes_per_step": n * 8 / E2E_STEPS, "d2h_bytes_per_step": n * 8 / E2E_STEPS,
            "steps_per_transfer": E2E_STEPS}
 
-    ens = _ensemble(torch)
+    ens = _ensemble(torch, with_oracle=(rank == 0 and ws == 1))
     adj = _adjoint(torch)
     if rank != 0:
         return
@@ -549,6 +595,7 @@ def run_ours(args):
         "fp64_df": {"what": "double-float precision (LB_FP64_DF): every value an unevaluated sum of two floats "
                             "(~48 bits), arithmetic on the FP32 units; errors in error_vs_oracle.fp64_df",
                     **df_line()},
+        "lattice_128": {"what": "the 128^3 spinodal lattice (seed 1), default step", **l128},
         "mrt": {"what": f"multiple-relaxation-time collision of f (lb_set_collision), tau = 1, "
                         f"tau_bulk = {MRT_RATES[0]}, tau_ghost = {MRT_RATES[1]}, on the default two-pass step",
                 "fp32_shifted": mrt_for("fp32_shifted"), "fp64": mrt_for("fp64")},
