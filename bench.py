@@ -655,6 +655,26 @@ def run_reference(args):
     }))
 
 
+def run_ensemble_only(args):
+    """The 64-lattice ensemble, ``--steps`` steps in one launch in each form
+    (a profiling case)."""
+    import torch
+    import paper_1405_6162_gb300 as lbpkg
+    from paper_1405_6162_gb300 import Batch
+    lbpkg.build()
+    specs = LI.ensemble(3, 64)
+    with Batch(specs, precision="fp32_shifted") as b:
+        b.set_launch(128, 0)
+        for form in ("general", "taug1"):
+            b.set_form(form)
+            for k, d in enumerate(specs):
+                b[k].init(LI.spinodal_phi0(d["nx"], d["ny"], d["nz"], seed=1000 + k))
+            b.run(args.steps)
+            b.sync()
+        torch.cuda.synchronize()
+        print(json.dumps({"only": "ensemble", "lattices": len(specs), "sites": b.sites, "steps": args.steps}))
+
+
 def run_step_only(args):
     """Just ``--steps`` timesteps of one lattice (a small case for profilers)."""
     import torch
@@ -695,8 +715,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--only", choices=["step"], default=None,
-                    help="run only timesteps of one lattice (profiling case)")
+    ap.add_argument("--only", choices=["step", "ensemble"], default=None,
+                    help="run only timesteps of one lattice, or of the 64-lattice ensemble in both forms "
+                         "(profiling cases)")
     ap.add_argument("--lattice", type=int, default=128, help="edge of the --only lattice")
     ap.add_argument("--precision", choices=["fp32_shifted", "fp64", "fp64_df"], default="fp32_shifted")
     ap.add_argument("--kernel", choices=["two_pass", "fused", "staged", "slab", "lag", "taug1"], default=None,
@@ -711,6 +732,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.only == "ensemble":
+        return run_ensemble_only(args)
     if args.only == "step":
         run_step_only(args)
     elif args.impl == "reference":
