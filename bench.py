@@ -221,7 +221,7 @@ def _ensemble(torch, with_oracle=True):
         if cfg is None:
             cfg, _ = tuning.autotune_batch(b, steps=10)
             init(b)
-        b.set_launch(*cfg)
+        tuning.apply_batch_config(b, cfg)
         b.run(500)                    # captures the graph
         b.sync()
         init(b)
@@ -237,7 +237,8 @@ def _ensemble(torch, with_oracle=True):
         out = {"lattices": len(specs), "sites": b.sites, "steps": 500, "seconds": t,
                "MLUPS": b.sites * 500 / t / 1e6, "precision": "fp32_shifted",
                "hbm_frac": b.sites * 500 * BYTES_PER_SITE["fp32_shifted"] / t / 1e9 / _peaks()[0],
-               "launch": {"threads": info[3], "ctas": info[2], "work_items": info[1]},
+               "launch": {"threads": info[3], "ctas": info[2], "work_items": info[1], "plan": b.plan,
+                          "groups": b.groups()},
                "graph_replays": 1}
         # every lattice has tau_g = 1: the same ensemble in the reduced form
         b.set_form("taug1")
@@ -246,7 +247,7 @@ def _ensemble(torch, with_oracle=True):
         if cfg1 is None:
             cfg1, _ = tuning.autotune_batch(b, steps=10)
             init(b)
-        b.set_launch(*cfg1)
+        tuning.apply_batch_config(b, cfg1)
         b.run(500)
         b.sync()
         init(b)
@@ -273,7 +274,8 @@ def _ensemble(torch, with_oracle=True):
                 errs.append({"lattice": list(dd), **{nm: float(np.abs(a - w).max() / np.abs(w).max())
                                                      for nm, a, w in zip(("rho", "u", "phi"), got, want)}})
         out["taug1"] = {"seconds": t1, "MLUPS": b.sites * 500 / t1 / 1e6, "error_vs_oracle_500_steps": errs,
-                        "launch": {"threads": info1[3], "ctas": info1[2], "work_items": info1[1]},
+                        "launch": {"threads": info1[3], "ctas": info1[2], "work_items": info1[1],
+                                   "plan": b.plan, "groups": b.groups()},
                         "hbm_frac": b.sites * 500 * BYTES_PER_SITE_TAUG1["fp32_shifted"] / t1 / 1e9 / _peaks()[0],
                         "what": "lb_batch_set_form(taug1): the tau_g = 1 reduced form for every lattice"}
         return out

@@ -337,9 +337,11 @@ int lb_adjoint_init(lb_ctx *c, const double *phi0, const double *u0, const doubl
  * An ensemble holds n lattices of any extents and parameters (one precision
  * for all).  lb_batch_run advances every lattice by nsteps timesteps with
  * one cooperative (co-resident) kernel launch that loops over the steps and
- * over a (lattice, block of sites) work list, with a grid-wide barrier
- * between the phi pass and the collide/stream pass; the launch is captured
- * in a CUDA graph (one per step count and parity) and replayed.  Per-site
+ * over a (lattice, block of sites) work list.  The grid is split into CTA
+ * groups by lb_batch_plan: each group advances its own lattices with a
+ * barrier of its CTAs alone between the phi pass and the collide/stream
+ * pass, so lattices never wait for one another.  The launch is captured in
+ * a CUDA graph (one per step count and parity) and replayed.  Per-site
  * arithmetic is exactly lb_step's.  Paper: the tunable thread-block size
  * TPB and per-thread work of TARGET_LAUNCH / TARGET_TLP, Sec. III.C. */
 typedef struct lb_batch lb_batch;
@@ -359,12 +361,12 @@ lb_ctx *lb_batch_lattice(lb_batch *b, int k);
 
 /* Advance every lattice by nsteps (>= 0), asynchronously after the work
  * queued on the ensemble's stream.  Errors: LB_ERR_INVALID, LB_ERR_CUDA;
- * a grid barrier that timed out is reported by lb_batch_sync (or lb_sync
+ * a group barrier that timed out is reported by lb_batch_sync (or lb_sync
  * of any member) as LB_ERR_TIMEOUT, after which the states are invalid
  * until re-initialised. */
 int lb_batch_run(lb_batch *b, int nsteps);
 
-/* Synchronise; LB_ERR_TIMEOUT if a grid barrier gave up since the last
+/* Synchronise; LB_ERR_TIMEOUT if a group barrier gave up since the last
  * check (the flag is then cleared). */
 int lb_batch_sync(lb_batch *b);
 
@@ -386,12 +388,37 @@ int lb_batch_set_form(lb_batch *b, int reduced);
 /* n lattices, work items per pass, CTAs in the grid, threads per CTA. */
 int lb_batch_size(const lb_batch *b, int *n, int *work_items, int *grid, int *threads);
 
-/* Bound (ns) of every grid-barrier wait (default 1e9). */
+/* CTA plan of the ensemble: 0 = the lb_batch_plan groups (default), 1 = one
+ * group of all CTAs walking the whole work list with a grid-wide barrier
+ * between the passes.  Same results either way.  Synchronises.  Paper: no
+ * counterpart. */
+int lb_batch_set_plan(lb_batch *b, int one_group);
+
+/* Number of CTA groups of the ensemble's current plan. */
+int lb_batch_groups(const lb_batch *b, int *ngroups);
+
+/* The CTA plan of an ensemble (host only; needs no GPU): n lattices with
+ * items[k] >= 1 work items per pass over ctas >= 1 co-resident CTAs.
+ *  - n <= ctas: lattice k is group k.  Every group starts with one CTA;
+ *    each further CTA goes to the group with the largest per-CTA share
+ *    ceil(items / CTAs) (ties to the lower index) until the CTAs run out or
+ *    every share is 1 (the CTAs left over stay idle).
+ *  - n > ctas: every CTA is a group of its own; the lattices, largest
+ *    first (stable), each go to the group with the least work so far (ties
+ *    to the lower group).
+ * Outputs (host arrays): group[k] (n entries) and, per group g, its first
+ * CTA cta0[g] and CTA count m[g] (min(n, ctas) entries; groups occupy
+ * consecutive CTAs from 0); *ngroups.  LB_ERR_INVALID on a bad argument. */
+int lb_batch_plan(int n, const long long *items, int ctas, int *group, int *cta0, int *m, int *ngroups);
+
+/* Bound (ns) of every group-barrier wait (default 1e9). */
 int lb_batch_set_wait_timeout(lb_batch *b, long long timeout_ns);
 
-/* Test hook: CTA 0 leaves before the first grid barrier, so every other
- * CTA's wait runs into its time bound (the timeout path without a GPU
- * fault).  0 restores normal operation.  Paper: no counterpart. */
+/* Test hook: the first CTA of the largest group leaves before the group's
+ * first barrier, so the group's other CTAs run into the time bound of their
+ * wait (the timeout path without a GPU fault); lb_batch_run returns
+ * LB_ERR_INVALID while the hook is on and no group has two CTAs.  0
+ * restores normal operation.  Paper: no counterpart. */
 int lb_batch_debug_skip_arrival(lb_batch *b, int enable);
 
 /* Extents and precision of c (any output may be NULL). */

@@ -10,6 +10,21 @@ from .lattice import PRECISIONS, Lattice, _torch, use_torch_allocator
 from . import lattice as _lattice
 
 
+def plan(items, ctas):
+    """The ensemble's CTA plan for lattices with ``items[k]`` work items per
+    pass over ``ctas`` co-resident CTAs (lb_batch_plan; host only, no GPU).
+    Returns (group of every lattice, [(first CTA, CTA count)] per group)."""
+    n = len(items)
+    it = (ctypes.c_longlong * max(n, 1))(*[int(x) for x in items])
+    ng_max = max(min(n, int(ctas)), 1)
+    group = (ctypes.c_int * max(n, 1))()
+    cta0 = (ctypes.c_int * ng_max)()
+    m = (ctypes.c_int * ng_max)()
+    ng = ctypes.c_int()
+    L.check(L.lib().lb_batch_plan(n, it, int(ctas), group, cta0, m, ctypes.byref(ng)), "lb_batch_plan")
+    return list(group[:n]), [(cta0[g], m[g]) for g in range(ng.value)]
+
+
 def _destroy(handle):
     try:
         L.lib().lb_batch_destroy(handle)
@@ -36,6 +51,7 @@ class Batch:
         self.specs = [dict(d) for d in lattices]
         self.precision = precision
         self.form = "general"
+        self.plan = "lattice"
         arr = (L.lb_params * len(self.specs))()
         for k, d in enumerate(self.specs):
             arr[k] = L.lb_params(d["nx"], d["ny"], d["nz"], d["tau"], d["tau_g"], d["rho0"], d["gamma"],
@@ -90,6 +106,18 @@ class Batch:
         v = [ctypes.c_int() for _ in range(4)]
         L.check(L.lib().lb_batch_size(self.handle, *[ctypes.byref(x) for x in v]), "lb_batch_size")
         return tuple(x.value for x in v)
+
+    def set_plan(self, plan: str = "lattice"):
+        """"lattice": CTA groups of :func:`plan` (default); "grid": one group
+        of all CTAs with a grid-wide barrier between the passes."""
+        L.check(L.lib().lb_batch_set_plan(self.handle, {"lattice": 0, "grid": 1}[plan]), "lb_batch_set_plan")
+        self.plan = plan
+
+    def groups(self) -> int:
+        """Number of CTA groups in the current plan (see :func:`plan`)."""
+        v = ctypes.c_int()
+        L.check(L.lib().lb_batch_groups(self.handle, ctypes.byref(v)), "lb_batch_groups")
+        return v.value
 
     def close(self):
         self._views.clear()

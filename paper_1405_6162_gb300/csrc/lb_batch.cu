@@ -2,22 +2,29 @@
 // parameters) advanced by one persistent launch, captured in a CUDA graph.
 //
 // Every lattice is an ordinary context (its own buffers and parameters).  The
-// work of one timestep over the whole ensemble is a list of (lattice, block
-// of sites) items; a grid of CTAs that all fit on the GPU at once (a
-// cooperative launch) walks that list twice per timestep -- the phi pass,
-// then the collide/stream pass -- with a grid-wide barrier after each, and
-// loops over the timesteps inside the kernel.  The per-site arithmetic is the
-// default step's (lb_site.cuh), or, for an ensemble whose lattices all have
-// tau_g = 1 and that was switched to the reduced form, the reduced form's two
-// passes (lb_t1.cuh): the collide pass over the same (lattice, block) items,
-// then the phi pass over (lattice, x block, warp group, z run) tiles.  The launch (with a reset of the barrier
-// state) is captured once per (steps, parity) into a CUDA graph and replayed.
-// The block size and CTAs per SM -- the paper's TPB and its per-thread work
-// (targetDP Sec. III.C) -- are the knobs the autotuner sets.
+// work of one timestep of a lattice is a list of (lattice, block of sites)
+// items.  A grid of CTAs that all fit on the GPU at once (a cooperative
+// launch) is split into groups: with no more lattices than CTAs each lattice
+// gets a group of its own, sized to its share of the work; otherwise every
+// CTA is a group holding several whole lattices.  A group's CTAs walk its
+// slice of the work list twice per timestep -- the phi pass, then the
+// collide/stream pass -- with a time-bounded barrier of that group alone
+// after each, and loop over the timesteps inside the kernel.  Lattices never
+// wait for one another, so no grid-wide barrier and its tail remain.  The
+// per-site arithmetic is the default step's (lb_site.cuh), or, for an
+// ensemble whose lattices all have tau_g = 1 and that was switched to the
+// reduced form, the reduced form's two passes (lb_t1.cuh): the collide pass
+// over the same (lattice, block) items, then the phi pass over (lattice, x
+// block, warp group, z run) tiles.  The launch (with a reset of the barrier
+// state) is captured once per (steps, parity) into a CUDA graph and
+// replayed.  The block size and CTAs per SM -- the paper's TPB and its
+// per-thread work (targetDP Sec. III.C) -- are the knobs the autotuner sets.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <map>
 #include <new>
+#include <queue>
 #include <utility>
 #include <vector>
 
@@ -32,12 +39,16 @@ namespace {
 
 // CTA size limit and CTAs per SM the register budget must allow (measured:
 // 3 x 256 threads FP32 and 2 x 256 FP64 beat the unconstrained allocation
-// by 11 % and 9 %)
+// by 11 % and 9 %; the FP32 reduced form gains another 6 % at 4 x 256,
+// 64 registers, where the general form loses 3 % to spills)
 #ifndef LBK_BATCH_MAXT32
 #define LBK_BATCH_MAXT32 256
 #endif
 #ifndef LBK_BATCH_MINB32
 #define LBK_BATCH_MINB32 3
+#endif
+#ifndef LBK_BATCH_MINB32_RED
+#define LBK_BATCH_MINB32_RED 4
 #endif
 #ifndef LBK_BATCH_MINB64
 #define LBK_BATCH_MINB64 2
@@ -63,6 +74,14 @@ struct GridBarrier {
     unsigned int gen;
 };
 
+// CTAs [cta0, cta0 + m) advance the lattices whose collide items are
+// work[wo, wo + wn) and whose reduced-form phi tiles are work_t1[to, to + tn)
+struct Group {
+    int cta0, m;
+    int wo, wn;
+    int to, tn;
+};
+
 __device__ __forceinline__ unsigned long long batch_ns()
 {
     unsigned long long t;
@@ -70,9 +89,9 @@ __device__ __forceinline__ unsigned long long batch_ns()
     return t;
 }
 
-// Grid-wide barrier of a co-resident grid.  Time-bounded: a CTA that waits
-// longer than timeout_ns (or sees that another CTA already gave up) sets the
-// error flag and returns false instead of hanging.
+// Barrier of nblocks co-resident CTAs (one group).  Time-bounded: a CTA that
+// waits longer than timeout_ns (or sees that another CTA already gave up)
+// sets the error flag and returns false instead of hanging.
 __device__ bool grid_sync(GridBarrier *bar, unsigned int nblocks, long long timeout_ns, unsigned int *err,
                           int *s_fail)
 {
@@ -106,21 +125,25 @@ __device__ bool grid_sync(GridBarrier *bar, unsigned int nblocks, long long time
 
 template <typename T, bool SH, bool RED>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? kBatchMaxThreads64 : kBatchMaxThreads,
-                                  sizeof(T) == 8 ? LBK_BATCH_MINB64 : LBK_BATCH_MINB32) k_batch(const LatDesc<T> *__restrict__ lats,
-                                                            const int2 *__restrict__ work, int nwork,
-                                                            const int4 *__restrict__ work_t1, int nwork_t1,
-                                                            int nsteps, int parity0, GridBarrier *bar,
-                                                            unsigned int *err, long long timeout_ns,
-                                                            int debug_skip_arrival)
+                                  sizeof(T) == 8 ? LBK_BATCH_MINB64 : (RED ? LBK_BATCH_MINB32_RED : LBK_BATCH_MINB32))
+    k_batch(const LatDesc<T> *__restrict__ lats, const int2 *__restrict__ work, const int4 *__restrict__ work_t1,
+            const Group *__restrict__ groups, const int *__restrict__ cta_group, int nsteps, int parity0,
+            GridBarrier *bars, unsigned int *err, long long timeout_ns, int skip_cta)
 {
     __shared__ int s_fail;
+    const int gi = cta_group[blockIdx.x];
+    if (gi < 0) return;   // a CTA the plan left without work
+    const Group G = groups[gi];
+    GridBarrier *bar = bars + gi;
+    const int r = blockIdx.x - G.cta0, wend = G.wo + G.wn;
     if (threadIdx.x == 0) s_fail = 0;
     if constexpr (RED) {
         constexpr int KY = PhiTile<T>::KY;
         const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int tend = G.to + G.tn;
         for (int t = 0; t < nsteps; t++) {
             const int a = (parity0 + t) & 1;
-            for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+            for (int w = G.wo + r; w < wend; w += G.m) {
                 const int2 it = work[w];
                 const LatDesc<T> &L = lats[it.x];
                 const long long s = (long long)it.y * blockDim.x + threadIdx.x;
@@ -128,43 +151,100 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kBatchMaxThreads64 : kBatchMa
                     t1_collide_site<T, SH, 7>(L.f[a], const_cast<T *>(L.g[a]), const_cast<T *>(L.f[1 - a]), L.p,
                                               L.nx, L.ny, L.nz, L.S, (int)s);
             }
-            if (debug_skip_arrival && blockIdx.x == 0) return;   // test hook: this CTA never arrives
-            if (!grid_sync(bar, gridDim.x, timeout_ns, err, &s_fail)) return;
-            for (int w = blockIdx.x; w < nwork_t1; w += gridDim.x) {
+            if ((int)blockIdx.x == skip_cta) return;   // test hook: this CTA never arrives
+            if (!grid_sync(bar, G.m, timeout_ns, err, &s_fail)) return;
+            for (int w = G.to + r; w < tend; w += G.m) {
                 const int4 it = work_t1[w];   // (lattice, x block, warp group, z run)
                 const LatDesc<T> &L = lats[it.x];
                 t1_phi_tile<T, KY>(L.g[a], const_cast<T *>(L.g[1 - a]), L.nx, L.ny, L.nz, L.kzc, L.S, it.y,
                                    (it.z * warps + warp) * KY, it.w, lane);
             }
-            if (!grid_sync(bar, gridDim.x, timeout_ns, err, &s_fail)) return;
+            if (!grid_sync(bar, G.m, timeout_ns, err, &s_fail)) return;
         }
     } else {
-    for (int t = 0; t < nsteps; t++) {
-        const int a = (parity0 + t) & 1;
-        for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
-            const int2 it = work[w];
-            const LatDesc<T> &L = lats[it.x];
-            const long long s = (long long)it.y * blockDim.x + threadIdx.x;
-            if (s < L.N) {
-                const Nbr n((int)s, L.nx, L.ny, L.nz);
-                L.phi[s] = phi_site(L.g[a], n, L.S);
+        for (int t = 0; t < nsteps; t++) {
+            const int a = (parity0 + t) & 1;
+            for (int w = G.wo + r; w < wend; w += G.m) {
+                const int2 it = work[w];
+                const LatDesc<T> &L = lats[it.x];
+                const long long s = (long long)it.y * blockDim.x + threadIdx.x;
+                if (s < L.N) {
+                    const Nbr n((int)s, L.nx, L.ny, L.nz);
+                    L.phi[s] = phi_site(L.g[a], n, L.S);
+                }
             }
-        }
-        if (debug_skip_arrival && blockIdx.x == 0) return;   // test hook: this CTA never arrives
-        if (!grid_sync(bar, gridDim.x, timeout_ns, err, &s_fail)) return;
-        for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
-            const int2 it = work[w];
-            const LatDesc<T> &L = lats[it.x];
-            const long long s = (long long)it.y * blockDim.x + threadIdx.x;
-            if (s < L.N) {
-                const Nbr n((int)s, L.nx, L.ny, L.nz);
-                collide_site<T, SH>(L.f[a], L.g[a], L.phi, const_cast<T *>(L.f[1 - a]),
-                                    const_cast<T *>(L.g[1 - a]), L.p, n, s, L.S);
+            if ((int)blockIdx.x == skip_cta) return;   // test hook: this CTA never arrives
+            if (!grid_sync(bar, G.m, timeout_ns, err, &s_fail)) return;
+            for (int w = G.wo + r; w < wend; w += G.m) {
+                const int2 it = work[w];
+                const LatDesc<T> &L = lats[it.x];
+                const long long s = (long long)it.y * blockDim.x + threadIdx.x;
+                if (s < L.N) {
+                    const Nbr n((int)s, L.nx, L.ny, L.nz);
+                    collide_site<T, SH>(L.f[a], L.g[a], L.phi, const_cast<T *>(L.f[1 - a]),
+                                        const_cast<T *>(L.g[1 - a]), L.p, n, s, L.S);
+                }
             }
+            if (!grid_sync(bar, G.m, timeout_ns, err, &s_fail)) return;
         }
-        if (!grid_sync(bar, gridDim.x, timeout_ns, err, &s_fail)) return;
     }
+}
+
+// The CTA plan.  n <= ctas: lattice k is group k; every group starts with
+// one CTA and each further CTA goes to the group whose largest per-CTA share
+// ceil(items / m) is the largest (ties to the lower index), until the CTAs
+// run out or no share can shrink (CTAs left over stay idle).  n > ctas: every
+// CTA is a group, and the lattices, largest first, each go to the group with
+// the least work so far (the longest-processing-time rule).
+int plan_groups(int n, const long long *items, int ctas, int *group, int *cta0, int *m, int *ngroups)
+{
+    if (n < 1 || ctas < 1 || !items || !group || !cta0 || !m || !ngroups) return LB_ERR_INVALID;
+    for (int k = 0; k < n; k++)
+        if (items[k] < 1) return LB_ERR_INVALID;
+    if (n <= ctas) {
+        std::vector<long long> mm(n, 1);
+        auto share = [&](int k) { return (items[k] + mm[k] - 1) / mm[k]; };
+        auto lower = [&](int a, int b) {   // a ranks below b in the queue
+            const long long sa = share(a), sb = share(b);
+            return sa != sb ? sa < sb : a > b;
+        };
+        std::priority_queue<int, std::vector<int>, decltype(lower)> q(lower);
+        for (int k = 0; k < n; k++) q.push(k);
+        for (int left = ctas - n; left > 0; left--) {
+            const int k = q.top();
+            if (share(k) <= 1) break;
+            q.pop();
+            mm[k]++;
+            q.push(k);
+        }
+        int c = 0;
+        for (int k = 0; k < n; k++) {
+            group[k] = k;
+            cta0[k] = c;
+            m[k] = (int)mm[k];
+            c += m[k];
+        }
+        *ngroups = n;
+        return LB_OK;
     }
+    std::vector<int> order(n);
+    for (int k = 0; k < n; k++) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return items[a] > items[b]; });
+    using Load = std::pair<long long, int>;   // (work so far, group)
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> q;
+    for (int g = 0; g < ctas; g++) q.push(Load(0, g));
+    for (int k : order) {
+        const Load l = q.top();
+        q.pop();
+        group[k] = l.second;
+        q.push(Load(l.first + items[k], l.second));
+    }
+    for (int g = 0; g < ctas; g++) {
+        cta0[g] = g;
+        m[g] = 1;
+    }
+    *ngroups = ctas;
+    return LB_OK;
 }
 
 }  // namespace
@@ -182,8 +262,13 @@ struct lb_batch {
     int nwork = 0;
     int4 *d_work_t1 = nullptr;                 // reduced form: phi-pass tiles
     int nwork_t1 = 0;
+    lbk::Group *d_groups = nullptr;            // the CTA plan
+    int *d_cta_group = nullptr;                // group of every CTA (-1: idle)
+    int ngroups = 0;
+    int one_group = 0;                         // lb_batch_set_plan: all CTAs in one group
     int reduced = 0;                           // all lattices in the tau_g = 1 reduced form
-    lbk::GridBarrier *d_bar = nullptr;
+    lbk::GridBarrier *d_bar = nullptr;         // one per group
+    int skip_cta = -1;                         // test hook: first CTA of the largest group
     unsigned int *d_err = nullptr;
     int threads = 256;                         // sites per work item = threads per CTA
     int ctas_per_sm = 0;                       // 0 = as many as fit
@@ -205,10 +290,24 @@ void drop_graphs(lb_batch *b)
 template <typename T, bool SH>
 int batch_tables(lb_batch *b)
 {
-    std::vector<lbk::LatDesc<T>> L(b->n);
-    std::vector<int2> work;
-    std::vector<int4> work_t1;
-    for (int k = 0; k < b->n; k++) {
+    // co-resident grid
+    int dev = 0, sms = 0, per_sm = 0;
+    int rc = lbk::cuda_status(cudaGetDevice(&dev));
+    if (!rc) rc = lbk::cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (!rc)
+        rc = lbk::cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, b->reduced ? lbk::k_batch<T, SH, true> : lbk::k_batch<T, SH, false>, b->threads, 0));
+    if (rc) return rc;
+    if (per_sm < 1) return LB_ERR_INVALID;
+    const int use = b->ctas_per_sm > 0 && b->ctas_per_sm < per_sm ? b->ctas_per_sm : per_sm;
+    b->grid = use * sms;
+
+    // per lattice: descriptor, collide items, reduced-form phi tiles
+    const int n = b->n;
+    std::vector<lbk::LatDesc<T>> L(n);
+    std::vector<std::vector<int4>> tiles(n);
+    std::vector<long long> nb(n);
+    for (int k = 0; k < n; k++) {
         lb_ctx *c = b->ctx[k];
         L[k].nx = c->p.nx;
         L[k].ny = c->p.ny;
@@ -222,48 +321,83 @@ int batch_tables(lb_batch *b)
         L[k].phi = (T *)c->phi;
         L[k].p = lbk::make_coll<T>(c->p);
         L[k].kzc = c->p.nz < lbk::kBatchT1Kzc ? c->p.nz : lbk::kBatchT1Kzc;
-        const long long nb = (c->N + b->threads - 1) / b->threads;
-        for (long long j = 0; j < nb; j++) work.push_back(make_int2(k, (int)j));
+        nb[k] = (c->N + b->threads - 1) / b->threads;
         if (b->reduced) {
             const int rows = (b->threads / 32) * lbk::PhiTile<T>::KY;   // y rows of one warp group
             const int gx = (c->p.nx + lbk::kPhiOut - 1) / lbk::kPhiOut, gy = (c->p.ny + rows - 1) / rows;
             const int gz = (c->p.nz + L[k].kzc - 1) / L[k].kzc;
             for (int z = 0; z < gz; z++)
                 for (int y = 0; y < gy; y++)
-                    for (int x = 0; x < gx; x++) work_t1.push_back(make_int4(k, x, y, z));
+                    for (int x = 0; x < gx; x++) tiles[k].push_back(make_int4(k, x, y, z));
         }
     }
+
+    // CTA groups, and the work lists ordered group by group
+    std::vector<int> lat_group(n), cta0(std::min(n, b->grid)), m(std::min(n, b->grid));
+    int ng = 0;
+    if (b->one_group) {
+        std::fill(lat_group.begin(), lat_group.end(), 0);
+        cta0[0] = 0;
+        m[0] = b->grid;
+        ng = 1;
+    } else {
+        rc = lbk::plan_groups(n, nb.data(), b->grid, lat_group.data(), cta0.data(), m.data(), &ng);
+        if (rc) return rc;
+    }
+    std::vector<lbk::Group> groups(ng);
+    std::vector<int> cta_group(b->grid, -1);
+    std::vector<int2> work;
+    std::vector<int4> work_t1;
+    for (int g = 0; g < ng; g++) {
+        lbk::Group &G = groups[g];
+        G.cta0 = cta0[g];
+        G.m = m[g];
+        G.wo = (int)work.size();
+        G.to = (int)work_t1.size();
+        for (int k = 0; k < n; k++) {
+            if (lat_group[k] != g) continue;
+            for (long long j = 0; j < nb[k]; j++) work.push_back(make_int2(k, (int)j));
+            work_t1.insert(work_t1.end(), tiles[k].begin(), tiles[k].end());
+        }
+        G.wn = (int)work.size() - G.wo;
+        G.tn = (int)work_t1.size() - G.to;
+        for (int i = 0; i < G.m; i++) cta_group[G.cta0 + i] = g;
+    }
+
     cudaFree(b->d_lats);
     cudaFree(b->d_work);
     cudaFree(b->d_work_t1);
+    cudaFree(b->d_groups);
+    cudaFree(b->d_cta_group);
+    cudaFree(b->d_bar);
     b->d_lats = nullptr;
     b->d_work = nullptr;
     b->d_work_t1 = nullptr;
-    int rc = lbk::cuda_status(cudaMalloc(&b->d_lats, sizeof(lbk::LatDesc<T>) * b->n));
-    if (!rc) rc = lbk::cuda_status(cudaMalloc(&b->d_work, sizeof(int2) * work.size()));
-    if (!rc) rc = lbk::cuda_status(cudaMemcpy(b->d_lats, L.data(), sizeof(lbk::LatDesc<T>) * b->n,
-                                              cudaMemcpyHostToDevice));
-    if (!rc) rc = lbk::cuda_status(cudaMemcpy(b->d_work, work.data(), sizeof(int2) * work.size(),
-                                              cudaMemcpyHostToDevice));
-    if (!rc && !work_t1.empty()) {
-        rc = lbk::cuda_status(cudaMalloc(&b->d_work_t1, sizeof(int4) * work_t1.size()));
-        if (!rc) rc = lbk::cuda_status(cudaMemcpy(b->d_work_t1, work_t1.data(), sizeof(int4) * work_t1.size(),
-                                                  cudaMemcpyHostToDevice));
-    }
+    b->d_groups = nullptr;
+    b->d_cta_group = nullptr;
+    b->d_bar = nullptr;
+    b->ngroups = 0;
+    auto upload = [&](void **dst, const void *src, size_t bytes) {
+        if (rc || !bytes) return;
+        rc = lbk::cuda_status(cudaMalloc(dst, bytes));
+        if (!rc) rc = lbk::cuda_status(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    };
+    upload(&b->d_lats, L.data(), sizeof(lbk::LatDesc<T>) * n);
+    upload((void **)&b->d_work, work.data(), sizeof(int2) * work.size());
+    upload((void **)&b->d_work_t1, work_t1.data(), sizeof(int4) * work_t1.size());
+    upload((void **)&b->d_groups, groups.data(), sizeof(lbk::Group) * groups.size());
+    upload((void **)&b->d_cta_group, cta_group.data(), sizeof(int) * cta_group.size());
+    if (!rc) rc = lbk::cuda_status(cudaMalloc(&b->d_bar, sizeof(lbk::GridBarrier) * ng));
+    if (rc) return rc;
     b->nwork = (int)work.size();
     b->nwork_t1 = (int)work_t1.size();
-    if (rc) return rc;
-    // co-resident grid
-    int dev = 0, sms = 0, per_sm = 0;
-    rc = lbk::cuda_status(cudaGetDevice(&dev));
-    if (!rc) rc = lbk::cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (!rc)
-        rc = lbk::cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, b->reduced ? lbk::k_batch<T, SH, true> : lbk::k_batch<T, SH, false>, b->threads, 0));
-    if (rc) return rc;
-    if (per_sm < 1) return LB_ERR_INVALID;
-    const int use = b->ctas_per_sm > 0 && b->ctas_per_sm < per_sm ? b->ctas_per_sm : per_sm;
-    b->grid = use * sms;
+    b->ngroups = ng;
+    b->skip_cta = -1;
+    for (int g = 0, best = 1; g < ng; g++)
+        if (groups[g].m > best) {
+            best = groups[g].m;
+            b->skip_cta = groups[g].cta0;
+        }
     return LB_OK;
 }
 
@@ -276,10 +410,11 @@ int tables(lb_batch *b)
 template <typename T, bool SH>
 int capture(lb_batch *b, int nsteps, int parity, cudaGraphExec_t *out)
 {
+    if (b->debug_skip && b->skip_cta < 0) return LB_ERR_INVALID;   // no group of two CTAs to test with
     cudaGraph_t graph = nullptr;
     int rc = lbk::cuda_status(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     if (rc) return rc;
-    cudaMemsetAsync(b->d_bar, 0, sizeof(lbk::GridBarrier), b->stream);
+    cudaMemsetAsync(b->d_bar, 0, sizeof(lbk::GridBarrier) * b->ngroups, b->stream);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)b->grid);
     cfg.blockDim = dim3((unsigned)b->threads);
@@ -291,10 +426,11 @@ int capture(lb_batch *b, int nsteps, int parity, cudaGraphExec_t *out)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const lbk::LatDesc<T> *lats = (const lbk::LatDesc<T> *)b->d_lats;
-    const cudaError_t le = cudaLaunchKernelEx(&cfg, b->reduced ? lbk::k_batch<T, SH, true> : lbk::k_batch<T, SH, false>,
-                                              lats, (const int2 *)b->d_work, b->nwork, (const int4 *)b->d_work_t1,
-                                              b->nwork_t1, nsteps, parity, b->d_bar, b->d_err, b->timeout_ns,
-                                              b->debug_skip);
+    const cudaError_t le =
+        cudaLaunchKernelEx(&cfg, b->reduced ? lbk::k_batch<T, SH, true> : lbk::k_batch<T, SH, false>, lats,
+                           (const int2 *)b->d_work, (const int4 *)b->d_work_t1, (const lbk::Group *)b->d_groups,
+                           (const int *)b->d_cta_group, nsteps, parity, b->d_bar, b->d_err, b->timeout_ns,
+                           b->debug_skip ? b->skip_cta : -1);
     const cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
     rc = lbk::cuda_status(le != cudaSuccess ? le : ce);
     if (!rc) rc = lbk::cuda_status(cudaGraphInstantiate(out, graph, 0));
@@ -335,6 +471,8 @@ void lb_batch_destroy(lb_batch *b)
     cudaFree(b->d_lats);
     cudaFree(b->d_work);
     cudaFree(b->d_work_t1);
+    cudaFree(b->d_groups);
+    cudaFree(b->d_cta_group);
     cudaFree(b->d_bar);
     cudaFree(b->d_err);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
@@ -366,7 +504,6 @@ int lb_batch_create(int n, const lb_params *p, void *cuda_stream, lb_batch **out
     if (!rc) rc = lbk::cuda_status(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
     if (!rc) rc = lbk::cuda_status(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
     if (!rc) rc = lbk::cuda_status(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
-    if (!rc) rc = lbk::cuda_status(cudaMalloc(&b->d_bar, sizeof(lbk::GridBarrier)));
     if (!rc) rc = lbk::cuda_status(cudaMalloc(&b->d_err, sizeof(unsigned int)));
     if (!rc) rc = lbk::cuda_status(cudaMemset(b->d_err, 0, sizeof(unsigned int)));
     if (!rc)
@@ -377,6 +514,33 @@ int lb_batch_create(int n, const lb_params *p, void *cuda_stream, lb_batch **out
         return rc;
     }
     *out = b;
+    return LB_OK;
+}
+
+int lb_batch_plan(int n, const long long *items, int ctas, int *group, int *cta0, int *m, int *ngroups)
+{
+    return lbk::plan_groups(n, items, ctas, group, cta0, m, ngroups);
+}
+
+int lb_batch_set_plan(lb_batch *b, int one_group)
+{
+    if (!b || (one_group != 0 && one_group != 1)) return LB_ERR_INVALID;
+    if (one_group == b->one_group) return LB_OK;
+    int rc = batch_sync(b);
+    if (rc) return rc;
+    b->one_group = one_group;
+    rc = tables(b);
+    if (rc) {
+        b->one_group = 1 - one_group;
+        tables(b);
+    }
+    return rc;
+}
+
+int lb_batch_groups(const lb_batch *b, int *ngroups)
+{
+    if (!b || !ngroups) return LB_ERR_INVALID;
+    *ngroups = b->ngroups;
     return LB_OK;
 }
 

@@ -102,33 +102,42 @@ def autotune(dims, precision, params, phi0, configs=None, steps=5, save=True, lo
 def _batch_key(batch) -> str:
     import hashlib
     h = hashlib.sha256(repr([sorted(d.items()) for d in batch.specs]).encode()).hexdigest()[:12]
-    return f"{_gpu_name()}|batch{len(batch)}:{h}|{batch.precision}|{getattr(batch, 'form', 'general')}"
+    return f"{_gpu_name()}|batch{len(batch)}:{h}|{batch.precision}|{getattr(batch, 'form', 'general')}|v2"
 
 
 def batch_candidates(precision):
+    """(threads per CTA, CTAs per SM, CTA plan) shapes to time."""
     threads = (128, 256)
-    return [(t, c) for t in threads for c in (0, 1, 2, 3)]
+    return [(t, c, p) for p in ("lattice", "grid") for t in threads for c in (0, 1, 2, 3)]
+
+
+def apply_batch_config(batch, config):
+    """Set a (threads, ctas_per_sm, plan) launch shape on an ensemble."""
+    t, c, p = config
+    batch.set_plan(p)
+    batch.set_launch(t, c)
 
 
 def autotune_batch(batch, steps=20, candidates=None, save=True, log=None):
-    """Time every (threads, ctas_per_sm) launch shape of an initialised
-    ensemble for ``steps`` steps, keep the fastest on the ensemble and in the
-    on-disk cache; returns (best, table).  Running the ensemble advances its
-    lattices: re-initialise them afterwards if their state matters."""
+    """Time every (threads, ctas_per_sm, plan) launch shape of an
+    initialised ensemble for ``steps`` steps, keep the fastest on the
+    ensemble and in the on-disk cache; returns (best, table).  Running the
+    ensemble advances its lattices: re-initialise them afterwards if their
+    state matters."""
     import torch
     table = []
     seen = set()
-    for t, c in candidates or batch_candidates(batch.precision):
+    for t, c, p in candidates or batch_candidates(batch.precision):
         try:
-            batch.set_launch(t, c)
+            apply_batch_config(batch, (t, c, p))
         except Exception as exc:
             if log:
-                log(f"skip {(t, c)}: {exc}")
+                log(f"skip {(t, c, p)}: {exc}")
             continue
         info = batch.info()
-        if (t, info[2]) in seen:          # same grid as a shape already timed
+        if (t, info[2], p) in seen:       # same grid as a shape already timed
             continue
-        seen.add((t, info[2]))
+        seen.add((t, info[2], p))
         batch.run(steps)                   # warm-up (captures the graph)
         torch.cuda.synchronize()
         s = torch.cuda.Event(enable_timing=True)
@@ -138,11 +147,11 @@ def autotune_batch(batch, steps=20, candidates=None, save=True, log=None):
         e.record()
         e.synchronize()
         dt = s.elapsed_time(e) / 1e3 / steps
-        table.append(((t, c), dt, info[2]))
+        table.append(((t, c, p), dt, info[2]))
         if log:
-            log(f"threads={t} ctas/SM={c} grid={info[2]}: {dt * 1e3:.3f} ms/step")
+            log(f"threads={t} ctas/SM={c} plan={p} grid={info[2]}: {dt * 1e3:.3f} ms/step")
     best = min(table, key=lambda r: r[1])
-    batch.set_launch(*best[0])
+    apply_batch_config(batch, best[0])
     batch.sync()
     if save:
         db = _load()
@@ -155,6 +164,6 @@ def autotune_batch(batch, steps=20, candidates=None, save=True, log=None):
 
 
 def batch_config(batch):
-    """Cached launch shape of this ensemble, or None."""
+    """Cached (threads, ctas_per_sm, plan) of this ensemble, or None."""
     hit = _load().get(_batch_key(batch))
     return tuple(hit["config"]) if hit else None

@@ -39,12 +39,15 @@ TOL_FP32_PER_STEP = {"rho": 2.5e-8, "u": 2.5e-8, "phi": 1e-7}
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_shifted"])
 @pytest.mark.parametrize("launch", [(256, 0), (128, 1), (64, 2)])
-def test_ensemble_matches_oracle_per_lattice(precision, launch):
+@pytest.mark.parametrize("plan", ["lattice", "grid"])
+def test_ensemble_matches_oracle_per_lattice(precision, launch, plan):
     from paper_1405_6162_gb300 import Batch
     specs = _small_ensemble(7)
     nsteps = 15
     with Batch(specs, precision=precision) as b:
+        b.set_plan(plan)
         b.set_launch(*launch)
+        assert b.groups() == (len(specs) if plan == "lattice" else 1)
         for k, d in enumerate(specs):
             b[k].init(_phi0(d, k))
         b.run(nsteps)
@@ -75,6 +78,36 @@ def test_split_runs_equal_one_run():
             assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
 
 
+def test_plans_give_identical_states():
+    """The CTA plan changes only which CTA runs which site: the per-lattice
+    groups, the one-group grid and a switch between them mid-run give
+    bit-identical states; with more lattices than CTAs (one CTA per SM)
+    groups hold several lattices."""
+    from paper_1405_6162_gb300 import Batch
+    specs = L.ensemble(16, 200, lo=2, hi=8)
+    out = []
+    for plans in (("lattice",), ("grid",), ("lattice", "grid"), ("grid", "lattice")):
+        with Batch(specs, precision="fp32_shifted") as b:
+            b.set_launch(32, 0)
+            for k, d in enumerate(specs):
+                b[k].init(_phi0(d, k))
+            for p in plans:
+                b.set_plan(p)
+                b.run(6 // len(plans))
+            out.append([b[k].get_state() for k in range(len(specs))])
+    with Batch(specs, precision="fp32_shifted") as b:
+        b.set_launch(256, 1)
+        ctas = b.info()[2]
+        assert ctas < len(specs) and b.groups() == ctas
+        for k, d in enumerate(specs):
+            b[k].init(_phi0(d, k))
+        b.run(6)
+        out.append([b[k].get_state() for k in range(len(specs))])
+    for other in out[1:]:
+        for (f0, g0), (f1, g1) in zip(out[0], other):
+            assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+
+
 def test_members_belong_to_the_ensemble():
     from paper_1405_6162_gb300 import Batch, LBError
     from paper_1405_6162_gb300 import _lib as LL
@@ -93,14 +126,16 @@ def test_members_belong_to_the_ensemble():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_shifted"])
-def test_grid_barrier_timeout_is_reported_and_recoverable(precision):
-    """One CTA leaves before the first grid barrier (test hook): every other
-    CTA's bounded wait gives up, the kernel ends, the host sees
+@pytest.mark.parametrize("plan", ["lattice", "grid"])
+def test_grid_barrier_timeout_is_reported_and_recoverable(precision, plan):
+    """One CTA leaves before its group's first barrier (test hook): the
+    group's other CTAs' bounded waits give up, the kernel ends, the host sees
     LB_ERR_TIMEOUT, and after re-initialisation the ensemble is exact."""
     from paper_1405_6162_gb300 import Batch, LBError
     from paper_1405_6162_gb300 import _lib as LL
     specs = _small_ensemble(10, n=3)
     with Batch(specs, precision=precision) as b:
+        b.set_plan(plan)
         b.set_wait_timeout(0.05)
         LL.check(LL.lib().lb_batch_debug_skip_arrival(b.handle, 1), "hook")
         for k, d in enumerate(specs):

@@ -52,10 +52,12 @@ def _check(b, specs, nsteps, precision):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_shifted"])
 @pytest.mark.parametrize("launch", [(256, 0), (128, 1), (64, 2)])
-def test_reduced_ensemble_matches_oracle(precision, launch):
+@pytest.mark.parametrize("plan", ["lattice", "grid"])
+def test_reduced_ensemble_matches_oracle(precision, launch, plan):
     from paper_1405_6162_gb300 import Batch
     specs = _ensemble(11)
     with Batch(specs, precision=precision) as b:
+        b.set_plan(plan)
         b.set_launch(*launch)
         b.set_form("taug1")
         for k, d in enumerate(specs):
