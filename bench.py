@@ -300,19 +300,25 @@ def _adjoint(torch):
         trajectory(phi0, params["kappa"], dims, params, T)
     torch.cuda.synchronize()
     t_fwd = _t.perf_counter() - t0
-    def forward_backward():
+    def forward_backward(segment=None):
         x = phi0.clone().requires_grad_(True)
         kap = torch.tensor(params["kappa"], dtype=torch.float64, device="cuda", requires_grad=True)
-        J = ((trajectory(x, kap, dims, params, T) - tgt) ** 2).sum()
+        J = ((trajectory(x, kap, dims, params, T, segment) - tgt) ** 2).sum()
         J.backward()
         return kap
 
-    forward_backward()                  # warm-up: first-call allocations of the reverse sweep
-    torch.cuda.synchronize()
-    t0 = _t.perf_counter()
-    kap = forward_backward()
-    torch.cuda.synchronize()
-    t_all = _t.perf_counter() - t0
+    def timed_fb(segment=None):
+        forward_backward(segment)       # warm-up: first-call allocations of the reverse sweep
+        torch.cuda.synchronize()
+        t0 = _t.perf_counter()
+        k = forward_backward(segment)
+        torch.cuda.synchronize()
+        return k, _t.perf_counter() - t0
+
+    kap, t_all = timed_fb()
+    # every state kept (one checkpoint per step, 2 x 19 N doubles each): no
+    # recomputation; the difference is what sqrt(T) checkpointing costs
+    kap_all, t_store = timed_fb(1)
     # dJ/dkappa against central differences of the forward alone, Richardson
     # extrapolated (J'' is large at these sizes, so plain O(h^2) differences
     # at h = 1e-5 still differ at ~1e-5)
@@ -332,6 +338,9 @@ def _adjoint(torch):
     g = kap.grad.item()
     return {"lattice": list(dims), "steps": T, "precision": "fp64", "checkpoints": "every 14 steps (~sqrt T)",
             "forward_s": t_fwd, "forward_backward_s": t_all, "ratio": t_all / t_fwd,
+            "forward_backward_every_state_kept_s": t_store,
+            "recompute_overhead": (t_all - t_store) / t_store,
+            "same_gradient_every_state_kept": bool(kap.grad.item() == kap_all.grad.item()),
             "dJ_dkappa": g, "dJ_dkappa_fd_richardson": fd_rich, "rel_diff_vs_fd": abs(g - fd_rich) / abs(fd_rich)}
 
 
