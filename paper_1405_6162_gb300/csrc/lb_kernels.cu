@@ -1,5 +1,5 @@
-// lb_kernels.cu -- initialisation, two-pass timestep, moments, state I/O and
-// the FP64 conservation reductions.
+// lb_kernels.cu -- the default two-pass timestep (phi pass, then the fused
+// pull-collide-stream pass).
 //
 // Storage convention: the context keeps the post-collision, pre-streaming
 // distributions A_i(x).  The post-streaming state of the model is the pull
@@ -14,34 +14,6 @@
 #include "lb_site.cuh"
 
 namespace lbk {
-
-// ------------------------------------------------------------------ init
-
-template <typename T, bool SH, int NP>
-__global__ void __launch_bounds__(256) k_init(const double *__restrict__ phi0,
-                                              const double *__restrict__ u0,
-                                              T *__restrict__ fa, T *__restrict__ ga,
-                                              Coll<double> p, int nx, int ny, int nz, long long S)
-{
-    const long long N = (long long)nx * ny * nz;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    const Nbr n(s, nx, ny, nz);
-    const double ph = phi0[s];
-    double dx, dy, dz, lap;
-    stencil_np<NP, double>(phi0, n, ph, dx, dy, dz, lap);
-    const double jx = u0 ? p.rho0 * u0[s] : 0.0;
-    const double jy = u0 ? p.rho0 * u0[N + s] : 0.0;
-    const double jz = u0 ? p.rho0 * u0[2 * N + s] : 0.0;
-    const double R = SH ? 0.0 : p.rho0;
-    // A_i(x - c_i) = feq_i(x): the first pull then yields the equilibrium.
-    equilibria<double, SH>(p, R, jx, jy, jz, ph, dx, dy, dz, lap,
-                           [&](int i, double fe, double ge) {
-                               const size_t o = (size_t)i * S + n.src(i);
-                               fa[o] = T(fe);
-                               ga[o] = T(ge);
-                           });
-}
 
 // ------------------------------------------------------------------ two-pass step
 
@@ -116,177 +88,9 @@ k_collide_pull_mrt(const T *__restrict__ fa, const T *__restrict__ ga, const T *
     }
 }
 
-// ------------------------------------------------------------------ moments / state
-
-template <typename T, bool SH>
-__global__ void __launch_bounds__(256) k_moments(const T *__restrict__ fa, const T *__restrict__ ga,
-                                                 double *__restrict__ rho, double *__restrict__ u,
-                                                 double *__restrict__ phi, double rho0, double hFx,
-                                                 double hFy, double hFz, int nx, int ny, int nz, long long S)
-{
-    const long long N = (long long)nx * ny * nz;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    const Nbr n(s, nx, ny, nz);
-    double f[Q], g[Q];
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        const size_t o = (size_t)i * S + n.src(i);
-        f[i] = double(fa[o]);
-        g[i] = double(ga[o]);
-    }
-    double R, jx, jy, jz;
-    density_moments(f, R, jx, jy, jz);
-    const double r = SH ? rho0 + R : R;
-    if (rho) rho[s] = r;
-    if (u) {
-        u[s] = (jx + hFx) / r;   // u = (sum f c + F/2) / rho
-        u[N + s] = (jy + hFy) / r;
-        u[2 * N + s] = (jz + hFz) / r;
-    }
-    if (phi) phi[s] = sum19(g);
-}
-
-// out[(i - i0)*N + s] = A_i(x - c_i) + shift_i, for i in [i0, i1)
-template <typename T>
-__global__ void __launch_bounds__(256) k_get_state(const T *__restrict__ a, double *__restrict__ out,
-                                                   int i0, int i1, double shift_rho0,
-                                                   int nx, int ny, int nz, long long S)
-{
-    const long long N = (long long)nx * ny * nz;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    const Nbr n(s, nx, ny, nz);
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        if (i < i0 || i >= i1) continue;
-        out[(size_t)(i - i0) * N + s] = double(a[(size_t)i * S + n.src(i)]) + weight(i) * shift_rho0;
-    }
-}
-
-// A_i(x - c_i) = in[(i - i0)*N + s] - shift_i, for i in [i0, i1)
-template <typename T>
-__global__ void __launch_bounds__(256) k_set_state(T *__restrict__ a, const double *__restrict__ in,
-                                                   int i0, int i1, double shift_rho0,
-                                                   int nx, int ny, int nz, long long S)
-{
-    const long long N = (long long)nx * ny * nz;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    const Nbr n(s, nx, ny, nz);
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        if (i < i0 || i >= i1) continue;
-        a[(size_t)i * S + n.src(i)] = T(in[(size_t)(i - i0) * N + s] - weight(i) * shift_rho0);
-    }
-}
-
-// ------------------------------------------------------------------ reductions
-// Totals over all sites need no pull: sum_x f_i(x, t) = sum_x A_i(x - c_i)
-// = sum_x A_i(x) on the periodic lattice.
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-template <int K>
-__device__ __forceinline__ void block_sum(double (&acc)[K], double *out)
-{
-    __shared__ double sh[kReduceThreads / 32][K];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; k++) acc[k] = warp_sum(acc[k]);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < K; k++) sh[wid][k] = acc[k];
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            double v = lane < kReduceThreads / 32 ? sh[lane][k] : 0.0;
-            v = warp_sum(v);
-            if (lane == 0) out[k] = v;
-        }
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kReduceThreads) k_reduce_partial(const T *__restrict__ fa,
-                                                                   const T *__restrict__ ga,
-                                                                   long long N, long long S, int g_rows,
-                                                                   double *__restrict__ partial)
-{
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < N;
-         s += (long long)gridDim.x * blockDim.x) {
-        double f[Q], g[Q];
-#pragma unroll
-        for (int i = 0; i < Q; i++) {
-            f[i] = double(fa[(size_t)i * S + s]);
-            g[i] = i < g_rows ? double(ga[(size_t)i * S + s]) : 0.0;   // reduced form: phi in row 0
-        }
-        double R, jx, jy, jz;
-        density_moments(f, R, jx, jy, jz);
-        acc[0] += R;
-        acc[1] += jx;
-        acc[2] += jy;
-        acc[3] += jz;
-        acc[4] += sum19(g);
-    }
-    block_sum<5>(acc, partial + 5 * blockIdx.x);
-}
-
-__global__ void __launch_bounds__(kReduceThreads) k_reduce_final(const double *__restrict__ partial,
-                                                                 int nblocks, double offset0,
-                                                                 double *__restrict__ out)
-{
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-#pragma unroll
-        for (int k = 0; k < 5; k++) acc[k] += partial[5 * b + k];
-    __shared__ double res[5];
-    block_sum<5>(acc, res);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        out[0] = res[0] + offset0;
-        for (int k = 1; k < 5; k++) out[k] = res[k];
-    }
-}
-
 // ------------------------------------------------------------------ launchers
 
 static inline unsigned grid_for(long long N, int tpb) { return (unsigned)((N + tpb - 1) / tpb); }
-
-template <typename T, bool SH, int NP>
-static void init_np(lb_ctx *c, const double *phi0_d, const double *u0_d)
-{
-    const int cur = c->buf.cur;
-    k_init<T, SH, NP><<<grid_for(c->N, 256), 256, 0, c->stream>>>(phi0_d, u0_d, (T *)c->buf.f[cur],
-                                                                  (T *)c->buf.g[cur], make_coll<double>(c->p),
-                                                                  c->p.nx, c->p.ny, c->p.nz, c->S);
-}
-
-template <typename T, bool SH>
-static void init_t(lb_ctx *c, const double *phi0_d, const double *u0_d)
-{
-    if (c->npts == 19)
-        init_np<T, SH, 19>(c, phi0_d, u0_d);
-    else if (c->npts == 27)
-        init_np<T, SH, 27>(c, phi0_d, u0_d);
-    else
-        init_np<T, SH, 7>(c, phi0_d, u0_d);
-}
-
-int launch_init(lb_ctx *c, const double *phi0_d, const double *u0_d)
-{
-    return by_precision(c, [&](auto P) {
-        init_t<typename decltype(P)::T, decltype(P)::SH>(c, phi0_d, u0_d);
-        return check_launch();
-    });
-}
 
 template <typename T, bool SH, int NP>
 static int two_pass(lb_ctx *c, int nsteps)
@@ -336,84 +140,6 @@ static int two_pass_t(lb_ctx *c, int nsteps)
 int launch_step_two_pass(lb_ctx *c, int nsteps)
 {
     return by_precision(c, [&](auto P) { return two_pass_t<typename decltype(P)::T, decltype(P)::SH>(c, nsteps); });
-}
-
-int launch_moments(lb_ctx *c, double *rho, double *u, double *phi)
-{
-    const int cur = c->buf.cur;
-    const double hF[3] = {0.5 * c->force[0], 0.5 * c->force[1], 0.5 * c->force[2]};
-    const unsigned grid = grid_for(c->N, 256);
-    return by_precision(c, [&](auto P) {
-        using T = typename decltype(P)::T;
-        k_moments<T, decltype(P)::SH><<<grid, 256, 0, c->stream>>>((const T *)c->buf.f[cur], (const T *)c->buf.g[cur],
-                                                                  rho, u, phi, c->p.rho0, hF[0], hF[1], hF[2],
-                                                                  c->p.nx, c->p.ny, c->p.nz, c->S);
-        return check_launch();
-    });
-}
-
-// f or g, components [i0, i1), to out (i1 - i0 rows of N)
-static int get_rows(lb_ctx *c, int which, int i0, int i1, double *out)
-{
-    const int cur = c->buf.cur;
-    const unsigned grid = grid_for(c->N, 256);
-    const double shift = (which == 0 && c->p.precision == LB_FP32_SHIFTED) ? c->p.rho0 : 0.0;
-    const void *a = which == 0 ? c->buf.f[cur] : c->buf.g[cur];
-    return by_precision(c, [&](auto P) {
-        using T = typename decltype(P)::T;
-        k_get_state<T><<<grid, 256, 0, c->stream>>>((const T *)a, out, i0, i1, shift, c->p.nx, c->p.ny, c->p.nz,
-                                                     c->S);
-        return check_launch();
-    });
-}
-
-static int set_rows(lb_ctx *c, int which, int i0, int i1, const double *in)
-{
-    const int cur = c->buf.cur;
-    const unsigned grid = grid_for(c->N, 256);
-    const double shift = (which == 0 && c->p.precision == LB_FP32_SHIFTED) ? c->p.rho0 : 0.0;
-    void *a = which == 0 ? c->buf.f[cur] : c->buf.g[cur];
-    return by_precision(c, [&](auto P) {
-        using T = typename decltype(P)::T;
-        k_set_state<T><<<grid, 256, 0, c->stream>>>((T *)a, in, i0, i1, shift, c->p.nx, c->p.ny, c->p.nz, c->S);
-        return check_launch();
-    });
-}
-
-int launch_get_state(lb_ctx *c, double *f, double *g)
-{
-    int rc = LB_OK;
-    if (f) rc = get_rows(c, 0, 0, Q, f);
-    if (!rc && g) rc = get_rows(c, 1, 0, Q, g);
-    return rc;
-}
-
-int launch_set_state(lb_ctx *c, const double *f, const double *g)
-{
-    int rc = LB_OK;
-    if (f) rc = set_rows(c, 0, 0, Q, f);
-    if (!rc && g) rc = set_rows(c, 1, 0, Q, g);
-    return rc;
-}
-
-int launch_rows(lb_ctx *c, int which, int i0, int i1, double *buf, int dir)
-{
-    return dir == 0 ? get_rows(c, which, i0, i1, buf) : set_rows(c, which, i0, i1, buf);
-}
-
-int launch_reduce(lb_ctx *c, double *dev_out5)
-{
-    const int cur = c->buf.cur;
-    const double off = c->p.precision == LB_FP32_SHIFTED ? double(c->N) * c->p.rho0 : 0.0;
-    int rc = by_precision(c, [&](auto P) {
-        using T = typename decltype(P)::T;
-        k_reduce_partial<T><<<kReduceBlocks, kReduceThreads, 0, c->stream>>>(
-            (const T *)c->buf.f[cur], (const T *)c->buf.g[cur], c->N, c->S, c->reduced ? 1 : Q, c->partial);
-        return check_launch();
-    });
-    if (rc) return rc;
-    k_reduce_final<<<1, kReduceThreads, 0, c->stream>>>(c->partial, kReduceBlocks, off, dev_out5);
-    return check_launch();
 }
 
 }  // namespace lbk

@@ -13,6 +13,7 @@
 
 #include "d3q19.cuh"
 #include "lb_internal.cuh"
+#include "lb_moments.cuh"
 #include "lb_site.cuh"
 
 namespace lbk {
@@ -146,28 +147,17 @@ __global__ void __launch_bounds__(kGatherThreads) k_masked_moments(
     if (k >= total) return;
     const int s = idx[k];
     const Nbr n(s, nx, ny, nz);
-    double f[Q];
-#pragma unroll
-    for (int i = 0; i < Q; i++) f[i] = double(fa[(size_t)i * S + n.src(i)]);
-    double R, jx, jy, jz;
-    density_moments(f, R, jx, jy, jz);
-    const double r = SH ? rho0 + R : R;
-    if (rho) rho[k] = r;
-    if (u) {
-        u[k] = (jx + hFx) / r;
-        u[(size_t)total + k] = (jy + hFy) / r;
-        u[2 * (size_t)total + k] = (jz + hFz) / r;
-    }
-    if (phi) {
-        if (REDUCED) {
-            phi[k] = double(ga[s]);
-        } else {
-            double g[Q];
-#pragma unroll
-            for (int i = 0; i < Q; i++) g[i] = double(ga[(size_t)i * S + n.src(i)]);
-            phi[k] = sum19(g);
+    if (rho || u) {
+        double r, v[3];
+        site_rho_u<T, SH>(fa, n, S, rho0, hFx, hFy, hFz, r, v);
+        if (rho) rho[k] = r;
+        if (u) {
+            u[k] = v[0];
+            u[(size_t)total + k] = v[1];
+            u[2 * (size_t)total + k] = v[2];
         }
     }
+    if (phi) phi[k] = REDUCED ? double(ga[s]) : site_phi(ga, n, S);
 }
 
 // rows [i0, i1) of the post-streaming state A_i(x - c_i) + w_i shift at the
