@@ -81,6 +81,11 @@ def _prm(params, kind):
     return _arr(np.array(vals, dtype=dt), kind)
 
 
+def threads(kind: str = "omp") -> int:
+    """Threads the parallel loops of build ``kind`` use (1 for serial)."""
+    return int(_lib(kind).orc_threads())
+
+
 def velocity_set():
     """(c[19,3] int, w[19] float64) in the oracle's order."""
     c = np.zeros(57, dtype=np.int32)

@@ -47,6 +47,9 @@
  * which every field and parameter is "double complex" (every operation here is
  * analytic, so Im(L(p + ih))/h is dL/dp to rounding).
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -91,6 +94,16 @@ static long site(long x, long y, long z, int nx, int ny, int nz)
 }
 
 int orc_nvel(void) { return NV; }
+
+/* Threads the parallel loops of this build use (1 without OpenMP). */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 void orc_velocity_set(int *c, double *w)
 {
