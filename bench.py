@@ -80,7 +80,7 @@ def _peaks():
 
 
 # sources the default timestep's kernels are compiled from
-STEP_SOURCES = ("d3q19.cuh", "lb_site.cuh", "lb_coll.cuh", "lb_kernels.cu")
+STEP_SOURCES = ("d3q19.cuh", "lb_site.cuh", "lb_coll.cuh", "lb_pdl.cuh", "lb_kernels.cu")
 
 
 def _kernel_sha(sources=STEP_SOURCES):

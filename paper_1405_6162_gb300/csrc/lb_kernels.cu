@@ -11,16 +11,19 @@
 
 #include "d3q19.cuh"
 #include "lb_internal.cuh"
+#include "lb_pdl.cuh"
 #include "lb_site.cuh"
 
 namespace lbk {
 
 // ------------------------------------------------------------------ two-pass step
+// (both kernels launched with programmatic dependent launch, lb_pdl.cuh)
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_phi_pull(const T *__restrict__ ga, T *__restrict__ phi,
                                                   int nx, int ny, int nz, long long S)
 {
+    pdl_wait_then_release();
     const long long N = (long long)nx * ny * nz;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
@@ -52,6 +55,7 @@ __global__ void __launch_bounds__(256, LBK_K2_MINB(T, NP)) k_collide_pull(const 
                                                       T *__restrict__ fb, T *__restrict__ gb,
                                                       Coll<T> p, int nx, int ny, int nz, long long S)
 {
+    pdl_wait_then_release();
     const long long N = (long long)nx * ny * nz;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
@@ -66,6 +70,7 @@ k_collide_pull_mrt(const T *__restrict__ fa, const T *__restrict__ ga, const T *
                    T *__restrict__ fb, T *__restrict__ gb, Coll<T> p, Mrt<T> m, int nx, int ny, int nz,
                    long long S)
 {
+    pdl_wait_then_release();
     const long long N = (long long)nx * ny * nz;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
@@ -104,14 +109,16 @@ static int two_pass(lb_ctx *c, int nsteps)
         const int a = c->buf.cur, b = 1 - a;
         const T *fa = (const T *)c->buf.f[a], *ga = (const T *)c->buf.g[a];
         T *fb = (T *)c->buf.f[b], *gb = (T *)c->buf.g[b];
-        k_phi_pull<T><<<grid, 256, 0, c->stream>>>(ga, (T *)c->phi, nx, ny, nz, c->S);
-        if (mrt)
-            k_collide_pull_mrt<T, SH, NP><<<grid, 256, 0, c->stream>>>(fa, ga, (const T *)c->phi, fb, gb, p, m, nx,
-                                                                     ny, nz, c->S);
-        else
-            k_collide_pull<T, SH, NP><<<grid, 256, 0, c->stream>>>(fa, ga, (const T *)c->phi, fb, gb, p, nx, ny,
-                                                                 nz, c->S);
-        int rc = check_launch();
+        cudaError_t e = launch_pdl(k_phi_pull<T>, grid, 256, c->stream, ga, (T *)c->phi, nx, ny, nz, c->S);
+        if (e == cudaSuccess) {
+            if (mrt)
+                e = launch_pdl(k_collide_pull_mrt<T, SH, NP>, grid, 256, c->stream, fa, ga, (const T *)c->phi, fb, gb,
+                               p, m, nx, ny, nz, c->S);
+            else
+                e = launch_pdl(k_collide_pull<T, SH, NP>, grid, 256, c->stream, fa, ga, (const T *)c->phi, fb, gb, p,
+                               nx, ny, nz, c->S);
+        }
+        int rc = e != cudaSuccess ? cuda_status(e) : check_launch();
         if (rc) return rc;
         c->buf.cur = b;
     }

@@ -37,6 +37,7 @@
 
 #include "d3q19.cuh"
 #include "lb_internal.cuh"
+#include "lb_pdl.cuh"
 #include "lb_site.cuh"
 #include "lb_t1.cuh"
 
@@ -51,6 +52,7 @@ __global__ void __launch_bounds__(kT1Threads, sizeof(T) == 8 ? 2 : 3)
 k_t1_collide(const T *__restrict__ fa, T *__restrict__ ga /* level a: phi in, (gmh, u) out */, T *__restrict__ fb,
              Coll<T> p, int nx, int ny, int nz, long long S)
 {
+    pdl_wait_then_release();
     const long long N = (long long)nx * ny * nz;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
@@ -63,6 +65,7 @@ template <typename T, int KY>
 __global__ void __launch_bounds__(32 * kPhiWarps) k_t1_phi(const T *__restrict__ ga, T *__restrict__ gb, int nx,
                                                             int ny, int nz, int kzc, long long S)
 {
+    pdl_wait_then_release();
     t1_phi_tile<T, KY>(ga, gb, nx, ny, nz, kzc, S, blockIdx.x, (blockIdx.y * kPhiWarps + threadIdx.y) * KY,
                        blockIdx.z, threadIdx.x);
 }
@@ -192,11 +195,12 @@ int run_t1(lb_ctx *c, int nsteps)
     const dim3 pblock(32, kPhiWarps);
     for (int t = 0; t < nsteps; t++) {
         const int a = c->buf.cur, b = 1 - a;
-        k_t1_collide<T, SH, NP><<<grid, kT1Threads, 0, c->stream>>>((const T *)c->buf.f[a], (T *)c->buf.g[a],
-                                                                (T *)c->buf.f[b], p, nx, ny, nz, c->S);
-        k_t1_phi<T, KY><<<pgrid, pblock, 0, c->stream>>>((const T *)c->buf.g[a], (T *)c->buf.g[b], nx, ny, nz, kzc,
-                                                          c->S);
-        const int rc = check_launch();
+        cudaError_t e = launch_pdl(k_t1_collide<T, SH, NP>, grid, kT1Threads, c->stream, (const T *)c->buf.f[a],
+                                   (T *)c->buf.g[a], (T *)c->buf.f[b], p, nx, ny, nz, c->S);
+        if (e == cudaSuccess)
+            e = launch_pdl(k_t1_phi<T, KY>, pgrid, pblock, c->stream, (const T *)c->buf.g[a], (T *)c->buf.g[b], nx,
+                           ny, nz, kzc, c->S);
+        const int rc = e != cudaSuccess ? cuda_status(e) : check_launch();
         if (rc) return rc;
         c->buf.cur = b;
         c->m_valid = 1;
