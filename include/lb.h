@@ -388,28 +388,31 @@ int lb_batch_set_form(lb_batch *b, int reduced);
 /* n lattices, work items per pass, CTAs in the grid, threads per CTA. */
 int lb_batch_size(const lb_batch *b, int *n, int *work_items, int *grid, int *threads);
 
-/* CTA plan of the ensemble: 0 = the lb_batch_plan groups (default), 1 = one
- * group of all CTAs walking the whole work list with a grid-wide barrier
- * between the passes.  Same results either way.  Synchronises.  Paper: no
- * counterpart. */
-int lb_batch_set_plan(lb_batch *b, int one_group);
+/* CTA plan of the ensemble (lb_batch_plan's bins): 0 = a group of CTAs per
+ * lattice (default), 1 = one group of all CTAs walking the whole work list
+ * with a grid-wide barrier between the passes, k >= 2 = k groups of whole
+ * lattices balanced by work.  Same results for every plan.  Synchronises.
+ * Paper: no counterpart. */
+int lb_batch_set_plan(lb_batch *b, int bins);
 
 /* Number of CTA groups of the ensemble's current plan. */
 int lb_batch_groups(const lb_batch *b, int *ngroups);
 
 /* The CTA plan of an ensemble (host only; needs no GPU): n lattices with
  * items[k] >= 1 work items per pass over ctas >= 1 co-resident CTAs.
- *  - n <= ctas: lattice k is group k.  Every group starts with one CTA;
- *    each further CTA goes to the group with the largest per-CTA share
- *    ceil(items / CTAs) (ties to the lower index) until the CTAs run out or
- *    every share is 1 (the CTAs left over stay idle).
- *  - n > ctas: every CTA is a group of its own; the lattices, largest
- *    first (stable), each go to the group with the least work so far (ties
- *    to the lower group).
+ *  - The groups: bins = 0 and n <= ctas: lattice k is group k.  bins = 0
+ *    and n > ctas: ctas groups.  bins >= 1: min(bins, n, ctas) groups.  In
+ *    the last two cases the lattices, largest first (stable), each go to the
+ *    group with the least work so far (ties to the lower group).
+ *  - The CTAs: every group starts with one; each further CTA goes to the
+ *    group with the largest per-CTA share ceil(work / CTAs) (ties to the
+ *    lower index) until the CTAs run out or every share is 1 (the CTAs left
+ *    over stay idle).
  * Outputs (host arrays): group[k] (n entries) and, per group g, its first
  * CTA cta0[g] and CTA count m[g] (min(n, ctas) entries; groups occupy
  * consecutive CTAs from 0); *ngroups.  LB_ERR_INVALID on a bad argument. */
-int lb_batch_plan(int n, const long long *items, int ctas, int *group, int *cta0, int *m, int *ngroups);
+int lb_batch_plan(int n, const long long *items, int ctas, int bins, int *group, int *cta0, int *m,
+                  int *ngroups);
 
 /* Bound (ns) of every group-barrier wait (default 1e9). */
 int lb_batch_set_wait_timeout(lb_batch *b, long long timeout_ns);

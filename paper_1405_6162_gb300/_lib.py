@@ -86,7 +86,7 @@ SIGNATURES = {
     "lb_batch_size": (_I, [_P, _P, _P, _P, _P]),
     "lb_batch_groups": (_I, [_P, _P]),
     "lb_batch_set_plan": (_I, [_P, _I]),
-    "lb_batch_plan": (_I, [_I, _P, _I, _P, _P, _P, _P]),
+    "lb_batch_plan": (_I, [_I, _P, _I, _I, _P, _P, _P, _P]),
     "lb_batch_set_wait_timeout": (_I, [_P, ctypes.c_longlong]),
     "lb_batch_debug_skip_arrival": (_I, [_P, _I]),
     "lb_strerror": (ctypes.c_char_p, [_I]),

@@ -10,9 +10,10 @@ from .lattice import PRECISIONS, Lattice, _torch, use_torch_allocator
 from . import lattice as _lattice
 
 
-def plan(items, ctas):
+def plan(items, ctas, bins=0):
     """The ensemble's CTA plan for lattices with ``items[k]`` work items per
-    pass over ``ctas`` co-resident CTAs (lb_batch_plan; host only, no GPU).
+    pass over ``ctas`` co-resident CTAs and ``bins`` (0: a group per lattice;
+    k: k groups of whole lattices), lb_batch_plan (host only, no GPU).
     Returns (group of every lattice, [(first CTA, CTA count)] per group)."""
     n = len(items)
     it = (ctypes.c_longlong * max(n, 1))(*[int(x) for x in items])
@@ -21,7 +22,7 @@ def plan(items, ctas):
     cta0 = (ctypes.c_int * ng_max)()
     m = (ctypes.c_int * ng_max)()
     ng = ctypes.c_int()
-    L.check(L.lib().lb_batch_plan(n, it, int(ctas), group, cta0, m, ctypes.byref(ng)), "lb_batch_plan")
+    L.check(L.lib().lb_batch_plan(n, it, int(ctas), int(bins), group, cta0, m, ctypes.byref(ng)), "lb_batch_plan")
     return list(group[:n]), [(cta0[g], m[g]) for g in range(ng.value)]
 
 
@@ -107,10 +108,12 @@ class Batch:
         L.check(L.lib().lb_batch_size(self.handle, *[ctypes.byref(x) for x in v]), "lb_batch_size")
         return tuple(x.value for x in v)
 
-    def set_plan(self, plan: str = "lattice"):
-        """"lattice": CTA groups of :func:`plan` (default); "grid": one group
-        of all CTAs with a grid-wide barrier between the passes."""
-        L.check(L.lib().lb_batch_set_plan(self.handle, {"lattice": 0, "grid": 1}[plan]), "lb_batch_set_plan")
+    def set_plan(self, plan="lattice"):
+        """"lattice": a group of CTAs per lattice (default); "grid": one group
+        of all CTAs with a grid-wide barrier between the passes; an int k >= 2:
+        k groups of whole lattices balanced by work (see :func:`plan`)."""
+        bins = {"lattice": 0, "grid": 1}.get(plan, plan)
+        L.check(L.lib().lb_batch_set_plan(self.handle, int(bins)), "lb_batch_set_plan")
         self.plan = plan
 
     def groups(self) -> int:

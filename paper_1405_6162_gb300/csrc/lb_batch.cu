@@ -190,60 +190,77 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kBatchMaxThreads64 : kBatchMa
     }
 }
 
-// The CTA plan.  n <= ctas: lattice k is group k; every group starts with
-// one CTA and each further CTA goes to the group whose largest per-CTA share
-// ceil(items / m) is the largest (ties to the lower index), until the CTAs
-// run out or no share can shrink (CTAs left over stay idle).  n > ctas: every
-// CTA is a group, and the lattices, largest first, each go to the group with
-// the least work so far (the longest-processing-time rule).
-int plan_groups(int n, const long long *items, int ctas, int *group, int *cta0, int *m, int *ngroups)
+// Longest-processing-time rule: the lattices, largest first (stable), each
+// to the bin with the least work so far (ties to the lower bin).
+void lpt_bins(int n, const long long *items, int nbins, int *bin, std::vector<long long> &load)
 {
-    if (n < 1 || ctas < 1 || !items || !group || !cta0 || !m || !ngroups) return LB_ERR_INVALID;
-    for (int k = 0; k < n; k++)
-        if (items[k] < 1) return LB_ERR_INVALID;
-    if (n <= ctas) {
-        std::vector<long long> mm(n, 1);
-        auto share = [&](int k) { return (items[k] + mm[k] - 1) / mm[k]; };
-        auto lower = [&](int a, int b) {   // a ranks below b in the queue
-            const long long sa = share(a), sb = share(b);
-            return sa != sb ? sa < sb : a > b;
-        };
-        std::priority_queue<int, std::vector<int>, decltype(lower)> q(lower);
-        for (int k = 0; k < n; k++) q.push(k);
-        for (int left = ctas - n; left > 0; left--) {
-            const int k = q.top();
-            if (share(k) <= 1) break;
-            q.pop();
-            mm[k]++;
-            q.push(k);
-        }
-        int c = 0;
-        for (int k = 0; k < n; k++) {
-            group[k] = k;
-            cta0[k] = c;
-            m[k] = (int)mm[k];
-            c += m[k];
-        }
-        *ngroups = n;
-        return LB_OK;
-    }
     std::vector<int> order(n);
     for (int k = 0; k < n; k++) order[k] = k;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return items[a] > items[b]; });
-    using Load = std::pair<long long, int>;   // (work so far, group)
+    using Load = std::pair<long long, int>;   // (work so far, bin)
     std::priority_queue<Load, std::vector<Load>, std::greater<Load>> q;
-    for (int g = 0; g < ctas; g++) q.push(Load(0, g));
+    for (int g = 0; g < nbins; g++) q.push(Load(0, g));
+    load.assign(nbins, 0);
     for (int k : order) {
         const Load l = q.top();
         q.pop();
-        group[k] = l.second;
-        q.push(Load(l.first + items[k], l.second));
+        bin[k] = l.second;
+        load[l.second] = l.first + items[k];
+        q.push(Load(load[l.second], l.second));
     }
-    for (int g = 0; g < ctas; g++) {
-        cta0[g] = g;
-        m[g] = 1;
+}
+
+// CTAs of the groups with work load[g]: one each, then each further CTA to
+// the group whose per-CTA share ceil(load / CTAs) is largest (ties to the
+// lower index) until the CTAs run out or every share is 1.
+std::vector<long long> share_ctas(const std::vector<long long> &load, int ctas)
+{
+    const int ng = (int)load.size();
+    std::vector<long long> mm(ng, 1);
+    auto share = [&](int g) { return (load[g] + mm[g] - 1) / mm[g]; };
+    auto lower = [&](int a, int b) {   // a ranks below b in the queue
+        const long long sa = share(a), sb = share(b);
+        return sa != sb ? sa < sb : a > b;
+    };
+    std::priority_queue<int, std::vector<int>, decltype(lower)> q(lower);
+    for (int g = 0; g < ng; g++) q.push(g);
+    for (int left = ctas - ng; left > 0; left--) {
+        const int g = q.top();
+        if (share(g) <= 1) break;
+        q.pop();
+        mm[g]++;
+        q.push(g);
     }
-    *ngroups = ctas;
+    return mm;
+}
+
+// The CTA plan.  bins = 0: with n <= ctas lattice k is group k; with more
+// lattices than CTAs every CTA is a group, filled by the LPT rule.  bins >= 1:
+// min(bins, n, ctas) groups, filled with whole lattices by the LPT rule.
+// CTAs go to the groups by share_ctas.
+int plan_groups(int n, const long long *items, int ctas, int bins, int *group, int *cta0, int *m, int *ngroups)
+{
+    if (n < 1 || ctas < 1 || bins < 0 || !items || !group || !cta0 || !m || !ngroups) return LB_ERR_INVALID;
+    for (int k = 0; k < n; k++)
+        if (items[k] < 1) return LB_ERR_INVALID;
+    std::vector<long long> load;
+    int ng;
+    if (bins == 0 && n <= ctas) {
+        ng = n;
+        load.assign(items, items + n);
+        for (int k = 0; k < n; k++) group[k] = k;
+    } else {
+        ng = bins == 0 ? ctas : std::min(bins, std::min(n, ctas));
+        lpt_bins(n, items, ng, group, load);
+    }
+    const std::vector<long long> mm = share_ctas(load, ctas);
+    int c = 0;
+    for (int g = 0; g < ng; g++) {
+        cta0[g] = c;
+        m[g] = (int)mm[g];
+        c += m[g];
+    }
+    *ngroups = ng;
     return LB_OK;
 }
 
@@ -265,7 +282,7 @@ struct lb_batch {
     lbk::Group *d_groups = nullptr;            // the CTA plan
     int *d_cta_group = nullptr;                // group of every CTA (-1: idle)
     int ngroups = 0;
-    int one_group = 0;                         // lb_batch_set_plan: all CTAs in one group
+    int bins = 0;                              // lb_batch_set_plan: 0 = a group per lattice, k = k groups
     int reduced = 0;                           // all lattices in the tau_g = 1 reduced form
     lbk::GridBarrier *d_bar = nullptr;         // one per group
     int skip_cta = -1;                         // test hook: first CTA of the largest group
@@ -335,15 +352,8 @@ int batch_tables(lb_batch *b)
     // CTA groups, and the work lists ordered group by group
     std::vector<int> lat_group(n), cta0(std::min(n, b->grid)), m(std::min(n, b->grid));
     int ng = 0;
-    if (b->one_group) {
-        std::fill(lat_group.begin(), lat_group.end(), 0);
-        cta0[0] = 0;
-        m[0] = b->grid;
-        ng = 1;
-    } else {
-        rc = lbk::plan_groups(n, nb.data(), b->grid, lat_group.data(), cta0.data(), m.data(), &ng);
-        if (rc) return rc;
-    }
+    rc = lbk::plan_groups(n, nb.data(), b->grid, b->bins, lat_group.data(), cta0.data(), m.data(), &ng);
+    if (rc) return rc;
     std::vector<lbk::Group> groups(ng);
     std::vector<int> cta_group(b->grid, -1);
     std::vector<int2> work;
@@ -517,21 +527,22 @@ int lb_batch_create(int n, const lb_params *p, void *cuda_stream, lb_batch **out
     return LB_OK;
 }
 
-int lb_batch_plan(int n, const long long *items, int ctas, int *group, int *cta0, int *m, int *ngroups)
+int lb_batch_plan(int n, const long long *items, int ctas, int bins, int *group, int *cta0, int *m, int *ngroups)
 {
-    return lbk::plan_groups(n, items, ctas, group, cta0, m, ngroups);
+    return lbk::plan_groups(n, items, ctas, bins, group, cta0, m, ngroups);
 }
 
-int lb_batch_set_plan(lb_batch *b, int one_group)
+int lb_batch_set_plan(lb_batch *b, int bins)
 {
-    if (!b || (one_group != 0 && one_group != 1)) return LB_ERR_INVALID;
-    if (one_group == b->one_group) return LB_OK;
+    if (!b || bins < 0) return LB_ERR_INVALID;
+    if (bins == b->bins) return LB_OK;
     int rc = batch_sync(b);
     if (rc) return rc;
-    b->one_group = one_group;
+    const int old = b->bins;
+    b->bins = bins;
     rc = tables(b);
     if (rc) {
-        b->one_group = 1 - one_group;
+        b->bins = old;
         tables(b);
     }
     return rc;

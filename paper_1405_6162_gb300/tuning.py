@@ -102,13 +102,13 @@ def autotune(dims, precision, params, phi0, configs=None, steps=5, save=True, lo
 def _batch_key(batch) -> str:
     import hashlib
     h = hashlib.sha256(repr([sorted(d.items()) for d in batch.specs]).encode()).hexdigest()[:12]
-    return f"{_gpu_name()}|batch{len(batch)}:{h}|{batch.precision}|{getattr(batch, 'form', 'general')}|v2"
+    return f"{_gpu_name()}|batch{len(batch)}:{h}|{batch.precision}|{getattr(batch, 'form', 'general')}|v3"
 
 
 def batch_candidates(precision):
     """(threads per CTA, CTAs per SM, CTA plan) shapes to time."""
     threads = (128, 256)
-    return [(t, c, p) for p in ("lattice", "grid") for t in threads for c in (0, 1, 2, 3)]
+    return [(t, c, p) for p in ("lattice", "grid", 4, 8, 16) for t in threads for c in (0, 1, 2, 3)]
 
 
 def apply_batch_config(batch, config):

@@ -1,9 +1,11 @@
 """The ensemble's CTA plan (lb_batch_plan), host logic only: no GPU.
 
-With no more lattices than CTAs every lattice is a group of its own, and the
-largest per-CTA share ceil(items / CTAs) must be the smallest any split of
-the CTAs allows (checked by brute force on small cases); with more lattices
-than CTAs every CTA is a group, filled by the longest-processing-time rule."""
+With no more lattices than CTAs and no bins every lattice is a group of its
+own, and the largest per-CTA share ceil(items / CTAs) must be the smallest
+any split of the CTAs allows (checked by brute force on small cases); with
+more lattices than CTAs, or with k bins, the groups are filled with whole
+lattices by the longest-processing-time rule and the CTAs split over the
+groups' work the same way."""
 import itertools
 import math
 import random
@@ -82,7 +84,40 @@ def test_more_lattices_than_ctas_longest_first():
     assert max(loads) <= sum(items) / 8 + max(items)
 
 
-@pytest.mark.parametrize("items,ctas", [([], 4), ([3, 0], 4), ([3, -1], 4), ([3], 0)])
-def test_invalid(items, ctas):
+@pytest.mark.parametrize("items,ctas,bins", [([], 4, 0), ([3, 0], 4, 0), ([3, -1], 4, 0), ([3], 0, 0), ([3], 4, -1)])
+def test_invalid(items, ctas, bins):
     with pytest.raises(LBError):
-        plan(items, ctas)
+        plan(items, ctas, bins)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bins_balance_whole_lattices(seed):
+    # k groups of whole lattices: the LPT bound on each group's work, and the
+    # CTA split over the groups' work is the integer min-max (brute force)
+    rng = random.Random(100 + seed)
+    n = rng.randint(3, 9)
+    items = [rng.randint(1, 30) for _ in range(n)]
+    bins = rng.randint(2, 3)
+    ctas = rng.randint(bins, 7)
+    group, groups = plan(items, ctas, bins)
+    _check_layout(items, ctas, group, groups)
+    assert len(groups) == min(bins, n, ctas)
+    loads = [0] * len(groups)
+    for k, g in enumerate(group):
+        loads[g] += items[k]
+    assert max(loads) <= sum(items) / len(groups) + max(items)
+    assert max(_shares(loads, groups)) == _best_max_share(loads, ctas)
+
+
+def test_one_bin_is_the_whole_grid():
+    items = [5, 9, 2, 7]
+    group, groups = plan(items, 12, 1)
+    assert group == [0, 0, 0, 0] and groups == [(0, 12)]
+    # fewer items than CTAs: one CTA per item, the rest idle
+    group, groups = plan([2, 1], 10, 1)
+    assert groups == [(0, 3)]
+
+
+def test_bins_capped_by_lattices_and_ctas():
+    assert len(plan([3, 4], 10, 5)[1]) == 2
+    assert len(plan([3, 4, 5, 6], 3, 8)[1]) == 3

@@ -39,7 +39,7 @@ TOL_FP32_PER_STEP = {"rho": 2.5e-8, "u": 2.5e-8, "phi": 1e-7}
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_shifted"])
 @pytest.mark.parametrize("launch", [(256, 0), (128, 1), (64, 2)])
-@pytest.mark.parametrize("plan", ["lattice", "grid"])
+@pytest.mark.parametrize("plan", ["lattice", "grid", 2])
 def test_ensemble_matches_oracle_per_lattice(precision, launch, plan):
     from paper_1405_6162_gb300 import Batch
     specs = _small_ensemble(7)
@@ -47,7 +47,7 @@ def test_ensemble_matches_oracle_per_lattice(precision, launch, plan):
     with Batch(specs, precision=precision) as b:
         b.set_plan(plan)
         b.set_launch(*launch)
-        assert b.groups() == (len(specs) if plan == "lattice" else 1)
+        assert b.groups() == {"lattice": len(specs), "grid": 1}.get(plan, plan)
         for k, d in enumerate(specs):
             b[k].init(_phi0(d, k))
         b.run(nsteps)
@@ -86,7 +86,7 @@ def test_plans_give_identical_states():
     from paper_1405_6162_gb300 import Batch
     specs = L.ensemble(16, 200, lo=2, hi=8)
     out = []
-    for plans in (("lattice",), ("grid",), ("lattice", "grid"), ("grid", "lattice")):
+    for plans in (("lattice",), ("grid",), (8,), ("lattice", "grid"), ("grid", 3), (5, "lattice")):
         with Batch(specs, precision="fp32_shifted") as b:
             b.set_launch(32, 0)
             for k, d in enumerate(specs):

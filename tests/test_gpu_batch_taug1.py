@@ -52,7 +52,7 @@ def _check(b, specs, nsteps, precision):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_shifted"])
 @pytest.mark.parametrize("launch", [(256, 0), (128, 1), (64, 2)])
-@pytest.mark.parametrize("plan", ["lattice", "grid"])
+@pytest.mark.parametrize("plan", ["lattice", "grid", 3])
 def test_reduced_ensemble_matches_oracle(precision, launch, plan):
     from paper_1405_6162_gb300 import Batch
     specs = _ensemble(11)
