@@ -248,3 +248,31 @@ def test_lagged_kernel_wait_timeout_is_reported_and_recoverable(precision):
     # phi0 amplitude 0.3 makes the stress terms O(1e-2): FP32 per-step bounds
     tol = TOL_FP64 if precision == "fp64" else {"rho": 1e-7, "u": 1e-7, "phi": 1e-6}
     _check_moments(got, mo, tol, fo)
+
+
+@pytest.mark.parametrize("precision,kernel", [("fp32_shifted", "two_pass"), ("fp64", "two_pass"),
+                                              ("fp64_df", "two_pass"), ("fp32_shifted", "taug1")])
+def test_dependent_launch_chain_with_interleaved_work(precision, kernel):
+    """The kernel pairs are chained with programmatic dependent launch.  A
+    run broken up by other work on the stream between steps (state and
+    moments read on the device, a torch kernel reading the state) gives the
+    bits of one uninterrupted run, and both match the oracle."""
+    import torch
+    dims = (24, 18, 11)
+    phi0 = L.spinodal_phi0(*dims, seed=77, amp=0.3)
+    with gpu_lattice(dims, P0, precision, kernel) as a, gpu_lattice(dims, P0, precision, kernel) as b:
+        a.init(phi0)
+        b.init(phi0)
+        a.step(9)
+        for _ in range(9):
+            b.step(1)
+            f, g = b.get_state(device=True)
+            assert torch.isfinite(f.sum() + g.sum()).item()
+            b.moments(device=True)
+        fa, ga = a.get_state()
+        fb, gb = b.get_state()
+        torch.cuda.synchronize()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+    fo, go = oracle.step(dims, P0, *oracle.init(dims, P0, phi0), 9)
+    tol = TOL_FP64 if precision != "fp32_shifted" else 2e-6
+    assert rel(to_oracle(fa), fo) <= tol and rel(to_oracle(ga), go) <= tol
