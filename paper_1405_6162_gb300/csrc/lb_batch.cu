@@ -4,9 +4,11 @@
 // Every lattice is an ordinary context (its own buffers and parameters).  The
 // work of one timestep of a lattice is a list of (lattice, block of sites)
 // items.  A grid of CTAs that all fit on the GPU at once (a cooperative
-// launch) is split into groups: with no more lattices than CTAs each lattice
-// gets a group of its own, sized to its share of the work; otherwise every
-// CTA is a group holding several whole lattices.  A group's CTAs walk its
+// launch) is split into groups (plan_groups): by default, with no more
+// lattices than CTAs, each lattice gets a group of its own, sized to its
+// share of the work (otherwise every CTA is a group holding several whole
+// lattices); the plan can also be k groups of whole lattices balanced by
+// work, k = 1 being the whole grid.  A group's CTAs walk its
 // slice of the work list twice per timestep -- the phi pass, then the
 // collide/stream pass -- with a time-bounded barrier of that group alone
 // after each, and loop over the timesteps inside the kernel.  Lattices never
