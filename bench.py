@@ -111,54 +111,117 @@ def _profile_value(name, key, need_current=True):
     return float(m_v.group(1))
 
 
+class _Nvml:
+    """Read-only NVML queries through ctypes (the driver's libnvidia-ml):
+    SM clock, its maximum and the active clock-event reasons.  Nothing is
+    set."""
+    SM = 1                                                     # NVML_CLOCK_SM
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, device_index):
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        got = False
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+            got = self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) == 0
+        except Exception:
+            got = False
+        if not got and self.lib.nvmlDeviceGetHandleByIndex_v2(device_index, ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        self.v = ctypes.c_uint()
+        self.r = ctypes.c_ulonglong()
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self.reasons_fn = fn or self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sample(self):
+        self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, ctypes.byref(self.v))
+        mhz = float(self.v.value)
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, ctypes.byref(self.v))
+        mx = float(self.v.value)
+        self.reasons_fn(self.h, ctypes.byref(self.r))
+        return mhz, mx, [name for bit, name in self.REASONS.items() if self.r.value & bit]
+
+
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons."""
+    """SM clocks and throttle reasons sampled during a timed region: NVML
+    every ~0.5 ms from a thread (nvidia-smi at 100 ms as a fallback)."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
+    PERIOD_S = 0.0005
 
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
+        self.rows = []
+        self.src = None
 
     def __enter__(self):
+        import threading
+        try:
+            nv = _Nvml(self.dev)
+            self.stop = threading.Event()
+
+            def run():
+                while not self.stop.is_set():
+                    self.rows.append(nv.sample())
+                    time.sleep(self.PERIOD_S)
+                self.rows.append(nv.sample())
+
+            self.rows.append(nv.sample())
+            self.thread = threading.Thread(target=run, daemon=True)
+            self.thread.start()
+            self.src = "nvml"
+            return self
+        except (OSError, AttributeError):
+            pass
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.src = "nvidia-smi"
         except OSError:
             self.proc = None
         return self
 
     def __exit__(self, *exc):
-        if self.proc:
+        if self.src == "nvml":
+            self.stop.set()
+            self.thread.join(timeout=5)
+        elif self.proc:
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                out, _ = self.proc.communicate(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                self.out = ""
+                out = ""
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for line in (out or "").strip().splitlines():
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    self.rows.append((float(parts[0]), float(parts[1]),
+                                      [names[k] for k, v in enumerate(parts[3:7]) if v.lower() == "active"]))
+                except ValueError:
+                    continue
         return False
 
     def summary(self):
-        if not self.proc:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        rows = []
-        for line in (self.out or "").strip().splitlines():
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 7:
-                continue
-            try:
-                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
-            except ValueError:
-                continue
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for _, _, fl in rows for k, v in enumerate(fl) if v.lower() == "active"})
-        sm = sorted(r[0] for r in rows)
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
-                "samples": len(rows)}
+        if not self.src:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock source"]}
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "source": self.src}
+        reasons = sorted({r for _, _, rs in self.rows for r in rs})
+        sm = sorted(r[0] for r in self.rows)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_min_mhz": sm[0], "sm_max_mhz": max(r[1] for r in self.rows),
+                "reasons": reasons, "samples": len(self.rows), "source": self.src}
 
 
 def _time_steps(lat, steps, torch):
@@ -170,6 +233,32 @@ def _time_steps(lat, steps, torch):
         e.record()
     torch.cuda.synchronize()
     return [s.elapsed_time(e) / 1e3 for s, e in ev]
+
+
+def _fp64_peak(torch, reps=5):
+    """FP64 FMA throughput (TFLOP/s) of this GPU, measured now: the best of
+    ``reps`` timed launches of liblb's FMA-only probe kernel (4 CTAs of 256
+    threads per SM, 8 independent chains per thread)."""
+    from paper_1405_6162_gb300 import _lib as LL
+    lib = LL.lib()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = 4 * sms
+    sink = torch.zeros(blocks, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    fl = ctypes.c_double()
+    best = 0.0
+    for it in range(reps + 2):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        LL.check(lib.lb_probe_fp64_fma(blocks, 8192, sink.data_ptr(), ctypes.c_void_p(stream.cuda_stream),
+                                       ctypes.byref(fl)), "lb_probe_fp64_fma")
+        e.record(stream)
+        e.synchronize()
+        if it >= 2:                                   # two warm-up launches
+            best = max(best, fl.value / (s.elapsed_time(e) / 1e3) / 1e12)
+    return {"tflops": best, "blocks": blocks, "threads": 256, "fmas_per_thread": 8 * 8192,
+            "how": "lb_probe_fp64_fma (FMA-only kernel), CUDA events, best of %d launches" % reps}
 
 
 def _oracle_errors(torch, params):
@@ -372,6 +461,7 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    fp64_peak = _fp64_peak(torch)
     results = {}
     for prec in ("fp32_shifted", "fp64"):
         cfg = tuning.bench_config(DIMS, prec)
@@ -528,7 +618,7 @@ def run_ours(args):
         else:
             # FP64 is bound by the FP64 pipe: flops per site from ncu counters
             fl = _profile_value(prof, "fp64_flops_per_site")
-            pk = _profile_value(prof, "fp64_peak_tflops", need_current=False)
+            pk = fp64_peak["tflops"]
             achieved = fl * n / r["t_launch"] / 1e12 if fl else None
             ins = _profile_value(prof, "fp64_instr_per_site")
             roof = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
@@ -537,7 +627,8 @@ def run_ours(args):
                     # instruction rate against the FMA-instruction peak (peak / 2)
                     "pipe_frac": (ins * n / r["t_launch"] / (pk * 1e12 / 2)) if (ins and pk) else None,
                     "traffic": _profile_value(prof, "dram_bytes_per_step"),
-                    "peak_kind": "measured FP64 FMA throughput (profiles/step_fp64_256cubed.md)",
+                    "peak_kind": "measured in this run: FP64 FMA throughput of lb_probe_fp64_fma",
+                    "peak_probe": fp64_peak,
                     "hbm_frac": BYTES_PER_SITE[prec] * n / r["t_launch"] / 1e9 / peak}
         return mlups, roof
 
@@ -562,7 +653,7 @@ def run_ours(args):
                "hbm_frac": achieved / peak, "achieved_gbs": achieved}
         if prec == "fp64":
             fl = _profile_value("step_isotropic_stencils_256cubed", f"fp64_flops_per_site_{npts}")
-            pk = _profile_value("step_fp64_256cubed", "fp64_peak_tflops", need_current=False)
+            pk = fp64_peak["tflops"]
             if fl and pk:
                 out["alu"] = {"achieved_tflops": fl * n / r["t_launch"] / 1e12, "peak_tflops": pk,
                               "frac": fl * n / r["t_launch"] / 1e12 / pk, "flops_per_site": fl}
@@ -576,7 +667,7 @@ def run_ours(args):
                "hbm_frac": achieved / peak, "achieved_gbs": achieved}
         if prec == "fp64":
             fl = _profile_value("step_mrt_256cubed", "fp64_flops_per_site")
-            pk = _profile_value("step_fp64_256cubed", "fp64_peak_tflops", need_current=False)
+            pk = fp64_peak["tflops"]
             if fl and pk:
                 out["alu"] = {"achieved_tflops": fl * n / r["t_launch"] / 1e12, "peak_tflops": pk,
                               "frac": fl * n / r["t_launch"] / 1e12 / pk, "flops_per_site": fl}
@@ -694,6 +785,15 @@ def run_ensemble_only(args):
         print(json.dumps({"only": "ensemble", "lattices": len(specs), "sites": b.sites, "steps": args.steps}))
 
 
+def run_fp64_peak_only(args):
+    """The FP64 FMA-throughput probe alone (the FP64 roofline's peak)."""
+    import torch
+    import paper_1405_6162_gb300 as lbpkg
+    lbpkg.build()
+    torch.cuda.set_device(_dist()[2])
+    print(json.dumps({"only": "fp64-peak", **_fp64_peak(torch, reps=max(3, args.steps))}))
+
+
 def run_step_only(args):
     """Just ``--steps`` timesteps of one lattice (a small case for profilers)."""
     import torch
@@ -734,9 +834,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--only", choices=["step", "ensemble"], default=None,
+    ap.add_argument("--only", choices=["step", "ensemble", "fp64-peak"], default=None,
                     help="run only timesteps of one lattice, or of the 64-lattice ensemble in both forms "
-                         "(profiling cases)")
+                         "(profiling cases), or the FP64 FMA-throughput probe")
     ap.add_argument("--lattice", type=int, default=128, help="edge of the --only lattice")
     ap.add_argument("--precision", choices=["fp32_shifted", "fp64", "fp64_df"], default="fp32_shifted")
     ap.add_argument("--kernel", choices=["two_pass", "fused", "staged", "slab", "lag", "taug1"], default=None,
@@ -753,6 +853,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.only == "ensemble":
         return run_ensemble_only(args)
+    if args.only == "fp64-peak":
+        return run_fp64_peak_only(args)
     if args.only == "step":
         run_step_only(args)
     elif args.impl == "reference":

@@ -295,8 +295,9 @@ int lb_debug_wait_skew(lb_ctx *c, unsigned long long skew);
  *           x + nx*(y + ny*z)) holding the post-collision values of the
  *           previous timestep, i.e. the post-streaming state is
  *           f_i(x, t) = fa[i*N + site(x - c_i)] (likewise g).
- *   fb, gb  output, same layout and convention for time t+1; must not
- *           alias the inputs (LB_ERR_INVALID).
+ *   fb, gb  output, same layout and convention for time t+1; neither may
+ *           share a byte with the other output or with an input
+ *           (LB_ERR_INVALID); the inputs may overlap each other.
  *   cuda_stream  stream the work is queued on (NULL = legacy default);
  *           the call returns before the work runs.
  * The arithmetic is lb_step's two-pass kernel pair.  The order parameter
@@ -325,6 +326,14 @@ int lb_step_fp64_noalloc(const lb_params *p, const double *fa, const double *ga,
  * recomputed from F(t)), the 7-point stencils and phi = sum g. */
 int lb_adjoint_step(lb_ctx *c, const double *f, const double *g, const double *af_in, const double *ag_in,
                     double *af_out, double *ag_out, double *dkappa);
+
+/* Start of the reverse sweep for a loss on phi_T = sum_i g_i(T) (the
+ * order parameter read out at time T): given dJ/dphi_T (device double[N]),
+ * writes F_bar(T) = (af, ag), device double[19][N] each: af = 0 and
+ * ag[i*N + s] = phi_bar[s] for every i (the transpose of the sum over i).
+ * Errors: LB_ERR_INVALID (NULL pointers, af == ag, not LB_FP64),
+ * LB_ERR_CUDA. */
+int lb_adjoint_seed(lb_ctx *c, const double *phi_bar, double *af, double *ag);
 
 /* Reverse of lb_init: given F_bar(0) = (af0, ag0), writes dJ/dphi0 to
  * phi0_bar (device double[N]) and adds the initialisation's dJ/dkappa to
@@ -423,6 +432,16 @@ int lb_batch_set_wait_timeout(lb_batch *b, long long timeout_ns);
  * LB_ERR_INVALID while the hook is on and no group has two CTAs.  0
  * restores normal operation.  Paper: no counterpart. */
 int lb_batch_debug_skip_arrival(lb_batch *b, int enable);
+
+/* Measurement helper: queue on cuda_stream one launch of `blocks` CTAs of
+ * 256 threads that do nothing but independent FP64 fused multiply-adds
+ * (8 chains of `iters` each per thread), for timing the FP64 pipe's peak
+ * with events around the call; *flops_out (host) receives the launch's
+ * flop count (2 per FMA).  sink: device double[blocks], written only if a
+ * chain's sum hits an impossible value (it keeps the work alive).  Errors:
+ * LB_ERR_INVALID, LB_ERR_CUDA.  Paper: no counterpart (the FP64 roofline
+ * of the timestep). */
+int lb_probe_fp64_fma(int blocks, long long iters, double *sink, void *cuda_stream, double *flops_out);
 
 /* Extents and precision of c (any output may be NULL). */
 int lb_get_info(const lb_ctx *c, int *nx, int *ny, int *nz, int *precision);

@@ -75,6 +75,7 @@ SIGNATURES = {
     "lb_debug_wait_skew": (_I, [_P, ctypes.c_ulonglong]),
     "lb_step_fp64_noalloc": (_I, [ctypes.POINTER(lb_params), _P, _P, _P, _P, _P]),
     "lb_adjoint_step": (_I, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "lb_adjoint_seed": (_I, [_P, _P, _P, _P]),
     "lb_adjoint_init": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "lb_batch_create": (_I, [_I, ctypes.POINTER(lb_params), _P, ctypes.POINTER(_P)]),
     "lb_batch_destroy": (None, [_P]),
@@ -89,6 +90,7 @@ SIGNATURES = {
     "lb_batch_plan": (_I, [_I, _P, _I, _I, _P, _P, _P, _P]),
     "lb_batch_set_wait_timeout": (_I, [_P, ctypes.c_longlong]),
     "lb_batch_debug_skip_arrival": (_I, [_P, _I]),
+    "lb_probe_fp64_fma": (_I, [_I, ctypes.c_longlong, _P, _P, _P]),
     "lb_strerror": (ctypes.c_char_p, [_I]),
     "lb_last_error": (ctypes.c_char_p, []),
 }

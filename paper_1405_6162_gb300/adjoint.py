@@ -6,7 +6,8 @@ to phi0 and kappa.  The forward keeps the state every ``segment`` steps
 (default ~sqrt(T) -- square-root checkpointing); the backward, segment by
 segment from the last, restores the checkpoint, recomputes and keeps that
 segment's states, then sweeps them in reverse with liblb's adjoint kernel
-pair (``lb_adjoint_step``) and finally the initialisation's reverse
+pair (``lb_adjoint_step``, started from ``lb_adjoint_seed``, the transpose
+of phi_T = sum_i g_i) and finally the initialisation's reverse
 (``lb_adjoint_init``).  Memory: about 2 sqrt(T) states of 38 N doubles.
 Argument marshalling only: all arithmetic is in liblb's kernels.
 """
@@ -51,8 +52,10 @@ class LBTrajectory(torch.autograd.Function):
         h = lat.handle
         n = lat.N
         dev = dict(device="cuda", dtype=torch.float64)
-        af = torch.zeros(19 * n, **dev)
-        ag = grad_phi_t.detach().to(**dev).contiguous().repeat(19)     # d(sum g)/dg_i = 1
+        af = torch.empty(19 * n, **dev)
+        ag = torch.empty(19 * n, **dev)
+        phi_bar = grad_phi_t.detach().to(**dev).contiguous()
+        L.check(lib.lb_adjoint_seed(h, _p(phi_bar), _p(af), _p(ag)), "lb_adjoint_seed")
         af2 = torch.empty_like(af)
         ag2 = torch.empty_like(ag)
         dk = torch.zeros(1, **dev)

@@ -251,6 +251,22 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_stencil(const double *__res
     }
 }
 
+// Adjoint of the read-out phi_T = sum_i g_i(T): f_bar = 0 and every
+// g_bar_i = dJ/dphi_T at the same site
+__global__ void __launch_bounds__(kAdjThreads) k_adj_seed(const double *__restrict__ phi_bar,
+                                                          double *__restrict__ af, double *__restrict__ ag,
+                                                          long long N)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const double pb = phi_bar[s];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        af[(size_t)i * N + s] = 0.0;
+        ag[(size_t)i * N + s] = pb;
+    }
+}
+
 // dkappa += sum of the per-CTA partials (one CTA, fixed order)
 __global__ void k_adj_kappa(const double *__restrict__ kpart, int nb, double *__restrict__ dkappa)
 {
@@ -289,6 +305,12 @@ int launch_adjoint_step(lb_ctx *c, const double *f, const double *g, const doubl
                                                             kpart, adj_params(c->p), nx, ny, nz);
     k_adj_stencil<false><<<nb, kAdjThreads, 0, c->stream>>>(aux, ag_out, nx, ny, nz);
     k_adj_kappa<<<1, kAdjThreads, 0, c->stream>>>(kpart, nb, dkappa);
+    return check_launch();
+}
+
+int launch_adjoint_seed(lb_ctx *c, const double *phi_bar, double *af, double *ag)
+{
+    k_adj_seed<<<adjoint_blocks(c->N), kAdjThreads, 0, c->stream>>>(phi_bar, af, ag, c->N);
     return check_launch();
 }
 

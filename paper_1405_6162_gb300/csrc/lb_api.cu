@@ -242,11 +242,20 @@ void lb_destroy(lb_ctx *c)
     delete c;
 }
 
+// the adjoint scratch, allocated on first use; on failure nothing is kept
 static int ensure_adj(lb_ctx *c)
 {
-    if (!c->adj) c->adj = (double *)dev_alloc(c, 6 * (size_t)c->N * sizeof(double));
-    if (!c->adj_part) c->adj_part = (double *)dev_alloc(c, (size_t)lbk::adjoint_blocks(c->N) * sizeof(double));
-    return c->adj && c->adj_part ? LB_OK : LB_ERR_NOMEM;
+    if (c->adj && c->adj_part) return LB_OK;
+    const size_t adj_bytes = 6 * (size_t)c->N * sizeof(double);
+    const size_t part_bytes = (size_t)lbk::adjoint_blocks(c->N) * sizeof(double);
+    if (!c->adj) c->adj = (double *)dev_alloc(c, adj_bytes);
+    if (!c->adj_part) c->adj_part = (double *)dev_alloc(c, part_bytes);
+    if (c->adj && c->adj_part) return LB_OK;
+    dev_free(c, c->adj, adj_bytes);
+    dev_free(c, c->adj_part, part_bytes);
+    c->adj = nullptr;
+    c->adj_part = nullptr;
+    return LB_ERR_NOMEM;
 }
 
 int lb_adjoint_step(lb_ctx *c, const double *f, const double *g, const double *af_in, const double *ag_in,
@@ -259,6 +268,12 @@ int lb_adjoint_step(lb_ctx *c, const double *f, const double *g, const double *a
     const int rc = ensure_adj(c);
     if (rc) return rc;
     return lbk::launch_adjoint_step(c, f, g, af_in, ag_in, af_out, ag_out, dkappa, c->adj, c->adj_part);
+}
+
+int lb_adjoint_seed(lb_ctx *c, const double *phi_bar, double *af, double *ag)
+{
+    if (!c || c->p.precision != LB_FP64 || !phi_bar || !af || !ag || af == ag) return LB_ERR_INVALID;
+    return lbk::launch_adjoint_seed(c, phi_bar, af, ag);
 }
 
 int lb_adjoint_init(lb_ctx *c, const double *phi0, const double *u0, const double *af0, const double *ag0,
@@ -511,12 +526,25 @@ int lb_set_state(lb_ctx *c, const double *f, const double *g, int ptr_kind)
 static int masked_prepare(lb_ctx *c, const unsigned char *mask, int ptr_kind, const unsigned char **mask_d,
                           long long *total)
 {
-    if (!c->mask_scratch) c->mask_scratch = (int *)dev_alloc(c, lbk::masked_scratch_ints(c->N) * sizeof(int));
-    if (!c->mask_scratch) return LB_ERR_NOMEM;
+    // the compaction buffers (and, for a host mask, its device copy) are
+    // allocated on first use; a failure keeps nothing allocated by this call
+    const size_t scratch_bytes = lbk::masked_scratch_ints(c->N) * sizeof(int);
+    const bool new_scratch = !c->mask_scratch, new_buf = ptr_kind == LB_HOST && !c->mask_buf;
+    if (new_scratch) c->mask_scratch = (int *)dev_alloc(c, scratch_bytes);
+    if (new_buf) c->mask_buf = (unsigned char *)dev_alloc(c, (size_t)c->N);
+    if (!c->mask_scratch || (ptr_kind == LB_HOST && !c->mask_buf)) {
+        if (new_scratch) {
+            dev_free(c, c->mask_scratch, scratch_bytes);
+            c->mask_scratch = nullptr;
+        }
+        if (new_buf) {
+            dev_free(c, c->mask_buf, (size_t)c->N);
+            c->mask_buf = nullptr;
+        }
+        return LB_ERR_NOMEM;
+    }
     int rc = LB_OK;
     if (ptr_kind == LB_HOST) {
-        if (!c->mask_buf) c->mask_buf = (unsigned char *)dev_alloc(c, (size_t)c->N);
-        if (!c->mask_buf) return LB_ERR_NOMEM;
         rc = copy(c, c->mask_buf, mask, (size_t)c->N, cudaMemcpyHostToDevice);
         *mask_d = c->mask_buf;
     } else {

@@ -477,7 +477,9 @@ void lb_batch_destroy(lb_batch *b)
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graphs(b);
     for (lb_ctx *c : b->ctx) {
-        lbk::release_from_batch(c);
+        // a member adopted into the ensemble shares its error flag (freed
+        // below); one created before a failure still owns its own
+        if (c->batch_owned) lbk::release_from_batch(c);
         lb_destroy(c);
     }
     cudaFree(b->d_lats);

@@ -135,6 +135,7 @@ int staged_validate(int precision, int block_x, int block_y, int z_chunk);
 int adjoint_blocks(long long N);
 int launch_adjoint_step(lb_ctx *c, const double *f, const double *g, const double *af_in, const double *ag_in,
                         double *af_out, double *ag_out, double *dkappa, double *aux, double *kpart);
+int launch_adjoint_seed(lb_ctx *c, const double *phi_bar, double *af, double *ag);
 int launch_adjoint_init(lb_ctx *c, const double *phi0, const double *u0, const double *af0, const double *ag0,
                         double *phi0_bar, double *dkappa, double *aux, double *kpart);
 

@@ -52,6 +52,13 @@ int scratch_address(double **out)
     return LB_OK;
 }
 
+// [a, a + bytes) and [b, b + bytes) share a byte
+bool overlap(const void *a, const void *b, size_t bytes)
+{
+    const char *x = static_cast<const char *>(a), *y = static_cast<const char *>(b);
+    return x < y + bytes && y < x + bytes;
+}
+
 bool valid(const lb_params *p)
 {
     if (!p || p->nx < 1 || p->ny < 1 || p->nz < 1) return false;
@@ -69,7 +76,12 @@ extern "C" int lb_step_fp64_noalloc(const lb_params *p, const double *fa, const 
     if (!valid(p) || !fa || !ga || !fb || !gb) return LB_ERR_INVALID;
     const long long N = (long long)p->nx * p->ny * p->nz;
     if (N > kNoAllocMaxSites) return LB_ERR_INVALID;   // lattice larger than the fixed scratch
-    if (fa == fb || ga == gb || fa == gb || ga == fb) return LB_ERR_INVALID;
+    // each output must share no byte with the other output or with an input
+    // (the inputs are only read and may overlap each other)
+    const size_t bytes = (size_t)lbk::Q * (size_t)N * sizeof(double);
+    if (overlap(fb, gb, bytes) || overlap(fb, fa, bytes) || overlap(fb, ga, bytes) || overlap(gb, fa, bytes) ||
+        overlap(gb, ga, bytes))
+        return LB_ERR_INVALID;
     double *phi = nullptr;
     const int rc = scratch_address(&phi);
     if (rc) return rc;

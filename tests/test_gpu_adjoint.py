@@ -133,3 +133,28 @@ def test_gradient_agrees_with_finite_differences_64cubed_T200():
         g = float((x.grad * v).sum())
         print("directional", seed, g, fd)
         assert abs(fd - g) <= 1e-6 * abs(g)
+
+
+def test_adjoint_seed_is_the_transpose_of_the_phi_readout():
+    """lb_adjoint_seed writes the adjoint of phi_T = sum_i g_i(T): f_bar = 0
+    and g_bar_i(x) = dJ/dphi_T(x) for every i, bit for bit; hence
+    <seed(p), (f, g)> = <p, sum_i g_i> for any state."""
+    import torch
+    from paper_1405_6162_gb300 import Lattice
+    from paper_1405_6162_gb300 import _lib as LL
+    dims = (9, 7, 5)
+    n = 315
+    pbar = torch.from_numpy(L.uniform(17, n, -1, 1)).cuda()
+    af = torch.full((19 * n,), 7.0, dtype=torch.float64, device="cuda")
+    ag = torch.empty_like(af)
+    with Lattice.from_params(dims, P0, precision="fp64") as lat:
+        LL.check(LL.lib().lb_adjoint_seed(lat.handle, pbar.data_ptr(), af.data_ptr(), ag.data_ptr()), "seed")
+        torch.cuda.synchronize()
+        assert LL.lib().lb_adjoint_seed(lat.handle, pbar.data_ptr(), af.data_ptr(), af.data_ptr()) == \
+            LL.LB_ERR_INVALID
+    assert bool((af == 0).all())
+    assert torch.equal(ag.view(19, n), pbar.expand(19, n))
+    g = torch.from_numpy(L.uniform(18, 19 * n, -1, 1)).cuda()
+    lhs = float((ag * g).sum())
+    rhs = float((pbar * g.view(19, n).sum(0)).sum())
+    assert abs(lhs - rhs) <= 1e-13 * abs(rhs)

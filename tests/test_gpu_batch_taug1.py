@@ -137,3 +137,24 @@ def test_grid_barrier_timeout_in_reduced_form():
         b.run(4)
         b.sync()
         _check(b, specs, 4, "fp32_shifted")
+
+
+def test_reduced_ensemble_64_uneven_lattices_500_steps_fp32():
+    """The 64-lattice workload in the reduced form, compared with the oracle
+    on the same nine lattices and bounds as the general form."""
+    from paper_1405_6162_gb300 import Batch
+    from tests.parity import ensemble_subsample, ensemble_workload, sites
+    from tests.test_gpu_batch import _check_ensemble_subsample
+    specs, phis = ensemble_workload()
+    with Batch(specs, precision="fp32_shifted") as b:
+        b.set_form("taug1")
+        for k in range(len(specs)):
+            b[k].init(phis[k])
+        r0 = [b[k].reduce() for k in range(len(specs))]
+        b.run(500)
+        b.sync()
+        r1 = [b[k].reduce() for k in range(len(specs))]
+        for k, d in enumerate(specs):
+            assert abs(r1[k][4] - r0[k][4]) <= 1e-6 * sites(d), (k, r1[k][4] - r0[k][4])
+        got = {k: b[k].moments() for k in ensemble_subsample(specs)}
+    _check_ensemble_subsample(specs, got, "reduced")

@@ -102,6 +102,27 @@ def test_kernels_agree(precision):
         assert np.abs(g - out[0][1]).max() <= 16 * ulp * np.abs(out[0][1]).max()
 
 
+@pytest.mark.parametrize("kernel,block", [("two_pass", (0, 0, 0)), ("fused", (0, 0, 0)), ("lag", (0, 0, 0))])
+def test_flow_u_against_its_max_fp64(kernel, block):
+    """A flow-dominated run: u ~ 1e-2 everywhere after 12 steps from a
+    non-equilibrium state with a random flow; u is compared with the oracle
+    against max|u| itself (not only against the size of its summands) at
+    the FP64 bar."""
+    dims = (20, 14, 11)
+    p = dict(P0, tau=0.8, tau_g=0.7)
+    f0, g0 = nonequilibrium_state(dims, p, seed=95)
+    (fo, go), mo = _oracle_run(dims, p, f0, g0, 12)
+    assert np.abs(mo[1]).max() > 5e-3
+    with gpu_lattice(dims, p, "fp64", kernel, block) as lat:
+        lat.set_state(to_abi(f0), to_abi(g0))
+        lat.step(12)
+        rho, u, phi = lat.moments()
+    e_u = rel(u, mo[1])
+    print(f"flow {kernel}: u vs max|u| = {np.abs(mo[1]).max():.3e}: {e_u:.3e}")
+    assert e_u <= TOL_FP64
+    assert rel(rho, mo[0]) <= TOL_FP64 and rel(phi, mo[2]) <= TOL_FP64
+
+
 def test_init_with_flow_matches_oracle():
     dims = (12, 10, 8)
     n = 960

@@ -70,6 +70,63 @@ def test_noalloc_step_matches_lb_step_on_two_calls_in_a_row():
             fa, ga = fb, gb
 
 
+def test_noalloc_step_matches_the_oracle_and_allocates_nothing():
+    """Two calls in a row against the FP64 oracle (an implementation that
+    shares nothing with the library), and the device's free memory unchanged
+    by calls made after the first one's set-up."""
+    import torch
+    import oracle
+    import paper_1405_6162_gb300 as lbpkg
+    from paper_1405_6162_gb300 import _lib as LL
+    from tests.parity import to_oracle
+    lbpkg.build()
+    oracle.build()
+    lib = LL.lib()
+    prm, p = _params()
+    f0, g0 = nonequilibrium_state(DIMS, p, seed=321)          # post-streaming state, oracle order
+    fo, go = oracle.step(DIMS, p, f0, g0, 2)
+    stream = torch.cuda.current_stream()
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    bufs = [cu(_roll(to_abi(f0), -1)), cu(_roll(to_abi(g0), -1))]
+    bufs += [torch.empty_like(bufs[0]) for _ in range(4)]
+    torch.cuda.synchronize()
+
+    def call(src, dst):
+        rc = lib.lb_step_fp64_noalloc(ctypes.byref(prm), bufs[src].data_ptr(), bufs[src + 1].data_ptr(),
+                                      bufs[dst].data_ptr(), bufs[dst + 1].data_ptr(),
+                                      ctypes.c_void_p(stream.cuda_stream))
+        assert rc == LL.LB_OK, lib.lb_strerror(rc)
+
+    call(0, 2)                                                # first call: set-up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    call(2, 4)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    f2 = to_oracle(_roll(bufs[4].cpu().numpy().reshape(19, -1), +1))
+    g2 = to_oracle(_roll(bufs[5].cpu().numpy().reshape(19, -1), +1))
+    assert rel(f2, fo) <= TOL_FP64, rel(f2, fo)
+    assert rel(g2, go) <= TOL_FP64, rel(g2, go)
+
+
+def test_noalloc_rejects_overlapping_outputs():
+    """Outputs that share any byte with each other or with an input are
+    refused before anything runs (the pointers below are never
+    dereferenced)."""
+    import paper_1405_6162_gb300 as lbpkg
+    from paper_1405_6162_gb300 import _lib as LL
+    lbpkg.build()
+    lib = LL.lib()
+    prm, _ = _params()
+    nb = 19 * DIMS[0] * DIMS[1] * DIMS[2] * 8
+    base = 1 << 30
+    fa, ga, fb, gb = base, base + 2 * nb, base + 4 * nb, base + 6 * nb
+    for args in ((fa, ga, fb, fb), (fa, ga, fb, fb + 8), (fa, ga, fa + nb - 8, gb), (fa, ga, fb, ga + 16),
+                 (fa, ga, gb - nb + 8, gb), (fa, ga, fa, gb)):
+        rc = lib.lb_step_fp64_noalloc(ctypes.byref(prm), *[ctypes.c_void_p(a) for a in args], None)
+        assert rc == LL.LB_ERR_INVALID, args
+
+
 def test_noalloc_rejects_lattices_beyond_its_scratch():
     import paper_1405_6162_gb300 as lbpkg
     from paper_1405_6162_gb300 import _lib as LL
