@@ -48,7 +48,7 @@ FALLBACK_HBM = 6800.0
 # kernels one timestep launches, per lb_set_kernel choice
 STEP_KERNELS = {"auto": "timestep = k_phi_pull + k_collide_pull (two launches)",
                 "two_pass": "timestep = k_phi_pull + k_collide_pull (two launches)",
-                "fused": "k_fused", "staged": "k_staged", "slab": "k_slab", "lag": "k_lag",
+                "fused": "k_fused", "staged": "k_staged", "slab": "k_slab", "lag": "k_lag", "bulk": "k_bulk",
                 "taug1": "timestep = k_t1_collide + k_t1_phi (two launches)"}
 
 
@@ -139,22 +139,23 @@ class _Nvml:
         fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
         self.reasons_fn = fn or self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
 
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, ctypes.byref(self.v))
+        self.max_mhz = float(self.v.value)
+
     def sample(self):
         self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, ctypes.byref(self.v))
         mhz = float(self.v.value)
-        self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, ctypes.byref(self.v))
-        mx = float(self.v.value)
         self.reasons_fn(self.h, ctypes.byref(self.r))
-        return mhz, mx, [name for bit, name in self.REASONS.items() if self.r.value & bit]
+        return mhz, self.max_mhz, [name for bit, name in self.REASONS.items() if self.r.value & bit]
 
 
 class Clocks:
     """SM clocks and throttle reasons sampled during a timed region: NVML
-    every ~0.5 ms from a thread (nvidia-smi at 100 ms as a fallback)."""
+    back to back from a thread (~1 ms a sample; nvidia-smi at 100 ms as a
+    fallback)."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
-    PERIOD_S = 0.0005
 
     def __init__(self, device_index):
         self.dev = device_index
@@ -171,7 +172,6 @@ class Clocks:
             def run():
                 while not self.stop.is_set():
                     self.rows.append(nv.sample())
-                    time.sleep(self.PERIOD_S)
                 self.rows.append(nv.sample())
 
             self.rows.append(nv.sample())
@@ -237,12 +237,12 @@ def _time_steps(lat, steps, torch):
 
 def _fp64_peak(torch, reps=5):
     """FP64 FMA throughput (TFLOP/s) of this GPU, measured now: the best of
-    ``reps`` timed launches of liblb's FMA-only probe kernel (4 CTAs of 256
-    threads per SM, 8 independent chains per thread)."""
+    ``reps`` timed launches of liblb's FMA-only probe kernel (8 CTAs of 256
+    threads per SM, 16 independent chains per thread)."""
     from paper_1405_6162_gb300 import _lib as LL
     lib = LL.lib()
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    blocks = 4 * sms
+    blocks = 8 * sms
     sink = torch.zeros(blocks, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     fl = ctypes.c_double()
@@ -251,13 +251,13 @@ def _fp64_peak(torch, reps=5):
         s = torch.cuda.Event(enable_timing=True)
         e = torch.cuda.Event(enable_timing=True)
         s.record(stream)
-        LL.check(lib.lb_probe_fp64_fma(blocks, 8192, sink.data_ptr(), ctypes.c_void_p(stream.cuda_stream),
+        LL.check(lib.lb_probe_fp64_fma(blocks, 4096, sink.data_ptr(), ctypes.c_void_p(stream.cuda_stream),
                                        ctypes.byref(fl)), "lb_probe_fp64_fma")
         e.record(stream)
         e.synchronize()
         if it >= 2:                                   # two warm-up launches
             best = max(best, fl.value / (s.elapsed_time(e) / 1e3) / 1e12)
-    return {"tflops": best, "blocks": blocks, "threads": 256, "fmas_per_thread": 8 * 8192,
+    return {"tflops": best, "blocks": blocks, "threads": 256, "fmas_per_thread": 16 * 4096,
             "how": "lb_probe_fp64_fma (FMA-only kernel), CUDA events, best of %d launches" % reps}
 
 
@@ -462,9 +462,18 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     fp64_peak = _fp64_peak(torch)
+    # the step kernel and launch shape of each precision: the autotuner's
+    # choice over the general-step kernels, tuned here on first use
+    tuned = {}
+    for prec in ("fp32_shifted", "fp64"):
+        t0 = time.perf_counter()
+        cached = tuning.cached_table(DIMS, prec) is not None
+        cfg = tuning.ensure_tuned(DIMS, prec, params, phi0)
+        tuned[prec] = {"config": list(cfg), "tuned_now": not cached, "seconds": time.perf_counter() - t0,
+                       "table": (tuning.cached_table(DIMS, prec) or {}).get("table")}
     results = {}
     for prec in ("fp32_shifted", "fp64"):
-        cfg = tuning.bench_config(DIMS, prec)
+        cfg = tuple(tuned[prec]["config"])
         with Lattice.from_params(DIMS, params, precision=prec) as lat:
             lat.set_kernel(*cfg)
             lat.init(phi0)
@@ -472,14 +481,16 @@ def run_ours(args):
             barrier()
             start = torch.cuda.Event(enable_timing=True)
             stop = torch.cuda.Event(enable_timing=True)
+            # clocks sampled over the timed steps and the per-launch timing
+            # that follows them (a ~1 ms sampler needs the longer window)
             with Clocks(local) as clk:
                 start.record()
                 lat.step(args.steps)
                 stop.record()
                 barrier()
+                # per-launch durations of the same kernel for the roofline
+                per = _time_steps(lat, max(20, min(args.steps, 40)), torch)
             wall = max_over_ranks(start.elapsed_time(stop) / 1e3, ws)
-            # per-launch durations of the same kernel for the roofline
-            per = _time_steps(lat, max(5, min(args.steps, 20)), torch)
             r = lat.reduce()
         t_launch = float(np.mean(per))
         results[prec] = dict(cfg=cfg, wall=wall, t_launch=t_launch, clocks=clk.summary(),
@@ -577,7 +588,7 @@ def run_ours(args):
     out_host = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
     e2e_iters = 2
     with Lattice.from_params(DIMS, params, precision=prec) as lat:
-        lat.set_kernel(*tuning.bench_config(DIMS, prec))
+        lat.set_kernel(*tuned[prec]["config"])
         lat.init(phi_host)
         lat.step(2)
         lbl = lat.handle
@@ -608,7 +619,8 @@ def run_ours(args):
         r = results[prec]
         mlups = ws * n * args.steps / r["wall"] / 1e6
         kernel = STEP_KERNELS.get(r["cfg"][0], r["cfg"][0])
-        prof = f"step_{prec}_256cubed"
+        # ncu summary of the kernel that ran (bulk: its own, with its sources listed)
+        prof = f"step_bulk_{prec}_256cubed" if r["cfg"][0] == "bulk" else f"step_{prec}_256cubed"
         if prec == "fp32_shifted":
             achieved = BYTES_PER_SITE[prec] * n / r["t_launch"] / 1e9
             roof = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -725,10 +737,15 @@ def run_ours(args):
                              "two-pass step; hbm_frac over the same 76-word algorithmic bytes",
                      **{f"{npts}pt": {prec: stencil_for(npts, prec) for prec in ("fp32_shifted", "fp64")}
                         for npts in (19, 27)}},
+        "autotune": {"what": "kernel and launch shape of the headline (fp32_shifted) and of the fp64 line, "
+                             "chosen by tuning.autotune over the general-step kernels (two_pass: threads per CTA, "
+                             "phi sites per thread; bulk: g slots, CTAs per y-cluster, planes per CTA; fused: "
+                             "tile and z run); table rows are [config, seconds per step]",
+                     **tuned},
         "ensemble": ens,
         "adjoint": adj,
         "e2e": e2e,
-        "gpu_launches": args.steps * (2 if r32["cfg"][0] in ("auto", "two_pass") else 1),
+        "gpu_launches": args.steps * (2 if r32["cfg"][0] in ("auto", "two_pass", "taug1") else 1),
         "cpu_baseline": cpu,
     }
     print(json.dumps(out))
@@ -800,7 +817,7 @@ def run_step_only(args):
     import paper_1405_6162_gb300 as lbpkg
     from paper_1405_6162_gb300 import Lattice, tuning
     lbpkg.build()
-    dims = (args.lattice,) * 3
+    dims = tuple(args.lattice) * 3 if len(args.lattice) == 1 else tuple(args.lattice)
     params = dict(LI.DEFAULT_PARAMS)
     cfg = tuning.bench_config(dims, args.precision)
     if args.kernel:
@@ -837,9 +854,10 @@ def main():
     ap.add_argument("--only", choices=["step", "ensemble", "fp64-peak"], default=None,
                     help="run only timesteps of one lattice, or of the 64-lattice ensemble in both forms "
                          "(profiling cases), or the FP64 FMA-throughput probe")
-    ap.add_argument("--lattice", type=int, default=128, help="edge of the --only lattice")
+    ap.add_argument("--lattice", type=int, nargs="+", default=[128],
+                    help="edge of the --only lattice, or its three extents")
     ap.add_argument("--precision", choices=["fp32_shifted", "fp64", "fp64_df"], default="fp32_shifted")
-    ap.add_argument("--kernel", choices=["two_pass", "fused", "staged", "slab", "lag", "taug1"], default=None,
+    ap.add_argument("--kernel", choices=["two_pass", "fused", "staged", "slab", "lag", "taug1", "bulk"], default=None,
                     help="override the tuned launch of the --only lattice")
     ap.add_argument("--block", type=int, nargs=3, default=(0, 0, 0), metavar=("BX", "BY", "ZC"))
     ap.add_argument("--stencil", type=int, choices=[7, 19, 27], default=7,

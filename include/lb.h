@@ -89,8 +89,15 @@ enum {
     LB_KERNEL_LAG = 5,      /* single pass, lagged pipeline: the CTA with
                                ticket c computes phi of site block c and
                                collides block c - D; bounded waits            */
-    LB_KERNEL_TAUG1 = 6     /* tau_g = 1 only: g kept as phi and (gmh, u),
+    LB_KERNEL_TAUG1 = 6,    /* tau_g = 1 only: g kept as phi and (gmh, u),
                                whose equilibria it is exactly; 49 words/site  */
+    LB_KERNEL_BULK = 7      /* single pass, one CTA per x-row marching z: the
+                               19 pulled g rows of each plane copied into
+                               shared memory by bulk asynchronous copies (g
+                               read from HBM once), phi rows shared along y
+                               in a thread-block cluster; FP64 or
+                               FP32-shifted, nx * element size a multiple of
+                               16 bytes, nx <= 256                            */
 };
 
 /* Collision of f, lb_set_collision(). */
@@ -211,8 +218,15 @@ int lb_set_state_masked(lb_ctx *c, const unsigned char *mask, const double *f, c
 /* Select the step kernel (LB_KERNEL_*) and its launch shape: block_x x
  * block_y threads per CTA and z_chunk planes per CTA of the fused, staged
  * and slab kernels (0 = library default for any of the three).  For
+ * LB_KERNEL_AUTO and LB_KERNEL_TWO_PASS block_x is the threads per CTA of
+ * both passes (a multiple of 32 up to 256; 0 = 256), block_y the sites per
+ * thread of the phi pass (1, 2 or 4; 0 = 1) and z_chunk must be 0.  For
  * LB_KERNEL_LAG block_x must be 0 or 256, block_y 0 or 1, and z_chunk is the
  * lag slack in site blocks beyond the stencil's reach (0 = default 128).
+ * For LB_KERNEL_BULK block_x is the number of shared-memory plane slots of
+ * g (3..8; 0 = 4 for FP32, 3 for FP64), block_y the CTAs per cluster along
+ * y (1, 2, 4 or 8, dividing ny; 0 = 4) and z_chunk the planes each CTA
+ * marches (0 = 32).
  * LB_KERNEL_TAUG1 requires tau_g == 1 (LB_ERR_INVALID otherwise) and
  * converts the stored state to its reduced form (selecting another kernel
  * converts back).  In that form lb_set_state keeps g only through
@@ -280,7 +294,9 @@ int lb_set_wait_timeout(lb_ctx *c, long long timeout_ns);
 
 /* Test hook: add `skew` to the lagged kernel's wait targets so that no wait
  * can be satisfied and every one runs into its time bound (the timeout path
- * without a GPU fault).  0 restores normal operation.  Paper: no
+ * without a GPU fault); with LB_KERNEL_BULK any non-zero skew makes every
+ * CTA's copy producer stop after its first plane, so the consumers' waits
+ * run into their bound.  0 restores normal operation.  Paper: no
  * counterpart. */
 int lb_debug_wait_skew(lb_ctx *c, unsigned long long skew);
 
@@ -435,9 +451,9 @@ int lb_batch_debug_skip_arrival(lb_batch *b, int enable);
 
 /* Measurement helper: queue on cuda_stream one launch of `blocks` CTAs of
  * 256 threads that do nothing but independent FP64 fused multiply-adds
- * (8 chains of `iters` each per thread), for timing the FP64 pipe's peak
- * with events around the call; *flops_out (host) receives the launch's
- * flop count (2 per FMA).  sink: device double[blocks], written only if a
+ * (16 chains of `iters` each per thread; iters a positive multiple of 4,
+ * at most 2^30), for timing the FP64 pipe's peak with events around the
+ * call; *flops_out (host) receives the launch's flop count (2 per FMA).  sink: device double[blocks], written only if a
  * chain's sum hits an impossible value (it keeps the work alive).  Errors:
  * LB_ERR_INVALID, LB_ERR_CUDA.  Paper: no counterpart (the FP64 roofline
  * of the timestep). */

@@ -35,6 +35,7 @@ LB_KERNEL_STAGED = 3
 LB_KERNEL_SLAB = 4
 LB_KERNEL_LAG = 5
 LB_KERNEL_TAUG1 = 6
+LB_KERNEL_BULK = 7
 
 
 class lb_params(ctypes.Structure):

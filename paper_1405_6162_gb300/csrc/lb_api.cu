@@ -345,6 +345,7 @@ int lb_step(lb_ctx *c, int nsteps)
     if (c->kernel == LB_KERNEL_STAGED) return lbk::launch_step_staged(c, nsteps);
     if (c->kernel == LB_KERNEL_SLAB) return lbk::launch_step_slab(c, nsteps);
     if (c->kernel == LB_KERNEL_LAG) return lbk::launch_step_lag(c, nsteps);
+    if (c->kernel == LB_KERNEL_BULK) return lbk::launch_step_bulk(c, nsteps);
     return lbk::launch_step_fused(c, nsteps);
 }
 
@@ -352,7 +353,7 @@ int lb_step(lb_ctx *c, int nsteps)
 static bool seven_point_only(int kernel)
 {
     return kernel == LB_KERNEL_FUSED || kernel == LB_KERNEL_STAGED || kernel == LB_KERNEL_SLAB ||
-           kernel == LB_KERNEL_LAG;
+           kernel == LB_KERNEL_LAG || kernel == LB_KERNEL_BULK;
 }
 
 static bool any_force(const double *F) { return F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0; }
@@ -394,14 +395,17 @@ int lb_set_stencil(lb_ctx *c, int points)
 int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk)
 {
     if (!c) return LB_ERR_INVALID;
-    if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_TAUG1 || c->batch_owned) return LB_ERR_INVALID;
+    if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_BULK || c->batch_owned) return LB_ERR_INVALID;
     if (block_x < 0 || block_y < 0 || z_chunk < 0) return LB_ERR_INVALID;
     if (c->npts != 7 && seven_point_only(kernel)) return LB_ERR_INVALID;
     if (c->p.precision == LB_FP64_DF && kernel != LB_KERNEL_AUTO && kernel != LB_KERNEL_TWO_PASS &&
         kernel != LB_KERNEL_TAUG1)
         return LB_ERR_INVALID;
     if (lbk::uses_mrt(c) && kernel != LB_KERNEL_AUTO && kernel != LB_KERNEL_TWO_PASS) return LB_ERR_INVALID;
-    if (kernel == LB_KERNEL_STAGED) {
+    if (kernel == LB_KERNEL_AUTO || kernel == LB_KERNEL_TWO_PASS) {
+        int rc = lbk::two_pass_validate(block_x, block_y, z_chunk);
+        if (rc) return rc;
+    } else if (kernel == LB_KERNEL_STAGED) {
         int rc = lbk::staged_validate(c->p.precision, block_x, block_y, z_chunk);
         if (rc) return rc;
     } else if (kernel == LB_KERNEL_TAUG1) {
@@ -411,6 +415,9 @@ int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk)
         if (rc) return rc;
     } else if (kernel == LB_KERNEL_SLAB) {
         int rc = lbk::slab_validate(c->p.precision, block_x, block_y, z_chunk);
+        if (rc) return rc;
+    } else if (kernel == LB_KERNEL_BULK) {
+        int rc = lbk::bulk_validate(c->p, block_x, block_y, z_chunk);
         if (rc) return rc;
     } else if (kernel == LB_KERNEL_FUSED) {
         int rc = lbk::fused_validate(c->p.precision, block_x, block_y, z_chunk);

@@ -112,6 +112,7 @@ int check_launch();
 // launchers (lb_kernels.cu); each returns an LB_* code
 int launch_init(lb_ctx *c, const double *phi0_d, const double *u0_d);
 int launch_step_two_pass(lb_ctx *c, int nsteps);
+int two_pass_validate(int block_x, int block_y, int z_chunk);   // threads per CTA, phi sites per thread
 // one FP64 two-pass timestep on raw buffers (component stride S, phi scratch
 // of N doubles supplied by the caller)
 int launch_two_pass_fp64_raw(const lb_params &p, const double *fa, const double *ga, double *phi, double *fb,
@@ -156,6 +157,10 @@ int launch_masked_rows(lb_ctx *c, long long total, const int *scratch, int which
 // lagged kernel (lb_lag.cu)
 int launch_step_lag(lb_ctx *c, int nsteps);
 int lag_validate(int block_x, int block_y, int z_chunk);
+
+// bulk-copy single-pass kernel (lb_bulk.cu)
+int launch_step_bulk(lb_ctx *c, int nsteps);
+int bulk_validate(const lb_params &p, int block_x, int block_y, int z_chunk);
 
 // slab kernel (lb_slab.cu)
 int launch_step_slab(lb_ctx *c, int nsteps);

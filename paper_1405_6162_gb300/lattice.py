@@ -18,7 +18,7 @@ from . import _lib as L
 PRECISIONS = {"fp64": L.LB_FP64, "fp32_shifted": L.LB_FP32_SHIFTED, "fp64_df": L.LB_FP64_DF}
 KERNELS = {"auto": L.LB_KERNEL_AUTO, "two_pass": L.LB_KERNEL_TWO_PASS, "fused": L.LB_KERNEL_FUSED,
            "staged": L.LB_KERNEL_STAGED, "slab": L.LB_KERNEL_SLAB, "lag": L.LB_KERNEL_LAG,
-           "taug1": L.LB_KERNEL_TAUG1}
+           "taug1": L.LB_KERNEL_TAUG1, "bulk": L.LB_KERNEL_BULK}
 
 _ALLOC_CB = None
 _FREE_CB = None

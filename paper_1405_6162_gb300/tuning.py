@@ -1,13 +1,24 @@
-"""Launch-shape selection for the fused step kernel.
+"""Kernel and launch-shape selection (autotuning) for one lattice and for
+ensembles.
 
 The paper tunes two knobs by hand -- the virtual vector length VVL (sites
 per thread) and the threads per block TPB (targetDP Sec. III.C and Sec. IV:
-VVL = 8 on the CPU, VVL = 2 on the K40).  Here the knobs of the fused kernel
-are the CTA tile (block_x x block_y sites of an x-y plane) and the number of
-z planes a CTA marches (z_chunk).  ``autotune`` times candidate shapes on the
-GPU through the C ABI and keeps the fastest in an on-disk cache keyed by GPU
-name, lattice extents and precision; ``bench_config`` returns the cached
-choice, or the library default when nothing was tuned.
+VVL = 8 on the CPU, VVL = 2 on the K40).  Here the tuner chooses, for one
+lattice, among the step kernels themselves and their launch shapes:
+
+* ``two_pass``: threads per CTA of both passes and sites per thread of the
+  phi pass (the VVL axis), ``("two_pass", tpb, vvl, 0)``;
+* ``bulk``: shared-memory plane slots of g, CTAs per y-cluster and planes per
+  CTA of the bulk-copy single pass, ``("bulk", slots, cluster, z_chunk)``;
+* ``fused``: CTA tile and z run of the shared-memory fused kernel;
+* ``taug1``: the tau_g = 1 reduced form, only when tau_g = 1 and asked for
+  (it keeps a different state, so it is a separate family).
+
+``autotune`` times every candidate on the GPU through the C ABI and keeps the
+fastest in an on-disk cache keyed by GPU name, lattice extents, precision
+and family set; ``bench_config`` returns the cached choice (or the library
+default), ``ensure_tuned`` tunes on first use.  ``autotune_batch`` does the
+same for an ensemble's (threads, CTAs per SM, CTA plan).
 """
 from __future__ import annotations
 
@@ -19,6 +30,9 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "auto
 
 # (kernel, block_x, block_y, z_chunk); 0 = library default
 DEFAULT = ("auto", 0, 0, 0)
+# kernels of the general step (any tau_g), the families the benchmark's
+# headline is tuned over
+GENERAL = ("two_pass", "bulk", "fused")
 
 
 def _gpu_name() -> str:
@@ -26,8 +40,8 @@ def _gpu_name() -> str:
     return torch.cuda.get_device_name() if torch.cuda.is_available() else "none"
 
 
-def _key(dims, precision) -> str:
-    return f"{_gpu_name()}|{dims[0]}x{dims[1]}x{dims[2]}|{precision}"
+def _key(dims, precision, families=GENERAL) -> str:
+    return f"{_gpu_name()}|{dims[0]}x{dims[1]}x{dims[2]}|{precision}|{'+'.join(families)}|v2"
 
 
 def _load() -> dict:
@@ -38,21 +52,53 @@ def _load() -> dict:
         return {}
 
 
-def bench_config(dims, precision):
-    """Launch configuration used for lattice ``dims`` in ``precision``."""
-    hit = _load().get(_key(dims, precision))
+def _save(key, entry):
+    db = _load()
+    db[key] = entry
+    os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+    tmp = CACHE + f".tmp{os.getpid()}"
+    with open(tmp, "w") as fh:
+        json.dump(db, fh, indent=1)
+    os.replace(tmp, CACHE)
+
+
+def bench_config(dims, precision, families=GENERAL):
+    """Launch configuration cached for lattice ``dims`` in ``precision``
+    over ``families``, else the library default."""
+    hit = _load().get(_key(dims, precision, families))
     return tuple(hit["config"]) if hit else DEFAULT
 
 
-def candidates(precision):
-    maxt = 256 if precision == "fp64" else 512
+def cached_table(dims, precision, families=GENERAL):
+    """The timed table behind a cached choice (None if not tuned)."""
+    return _load().get(_key(dims, precision, families))
+
+
+def _bulk_ok(dims, precision):
+    es = 8 if precision == "fp64" else 4
+    return precision in ("fp64", "fp32_shifted") and dims[0] <= 256 and (dims[0] * es) % 16 == 0
+
+
+def candidates(precision, dims=None, families=GENERAL, tau_g=None):
+    """Configurations to time for ``dims`` in ``precision``."""
     out = []
-    for bx in (32, 64, 128):
-        for by in (1, 2, 4, 8, 16):
-            if bx * by > maxt or bx * by < 64:
-                continue
-            for zc in (8, 16, 32, 64):
-                out.append(("fused", bx, by, zc))
+    if "two_pass" in families:
+        for tpb in (128, 256):
+            for vvl in (1, 2, 4):
+                out.append(("two_pass", tpb, vvl, 0))
+    if "bulk" in families and (dims is None or _bulk_ok(dims, precision)):
+        slots = (3, 4) if precision == "fp64" else (3, 4, 6)
+        for ng in slots:
+            for cy in (1, 2, 4, 8):
+                if dims is not None and (dims[1] % cy or cy > dims[1]):
+                    continue
+                for zc in (16, 32, 64):
+                    out.append(("bulk", ng, cy, zc))
+    if "fused" in families and precision != "fp64_df":
+        for bx, by, zc in ((32, 4, 32), (64, 2, 32), (32, 8, 64), (64, 4, 16)):
+            out.append(("fused", bx, by, zc))
+    if "taug1" in families and tau_g == 1.0:
+        out.append(("taug1", 0, 0, 0))
     return out
 
 
@@ -68,35 +114,45 @@ def time_config(lat, config, steps=5, warmup=2):
     lat.step(steps)
     e.record()
     e.synchronize()
+    lat.sync()
     return s.elapsed_time(e) / 1e3 / steps
 
 
-def autotune(dims, precision, params, phi0, configs=None, steps=5, save=True, log=None):
-    """Time every candidate shape on ``dims``; returns (best_config, table)."""
+def autotune(dims, precision, params, phi0, configs=None, families=GENERAL, steps=5, save=True, log=None):
+    """Time every candidate on ``dims``; returns (best_config, table).  The
+    table's rows are (config, seconds per step); configurations the library
+    refuses for this lattice are skipped."""
     from .lattice import Lattice
-    configs = configs or candidates(precision)
+    configs = configs or candidates(precision, dims, families, params.get("tau_g"))
     table = []
     with Lattice.from_params(dims, params, precision=precision) as lat:
         lat.init(phi0)
         for cfg in configs:
             try:
                 t = time_config(lat, cfg, steps=steps)
-            except Exception as exc:  # an invalid shape for this build
+            except Exception as exc:  # a shape this lattice or build refuses
                 if log:
                     log(f"skip {cfg}: {exc}")
                 continue
-            table.append((cfg, t))
+            table.append((tuple(cfg), t))
             if log:
                 log(f"{cfg} {t * 1e3:.3f} ms")
     best = min(table, key=lambda r: r[1])
     if save:
-        db = _load()
-        db[_key(dims, precision)] = {"config": list(best[0]), "seconds_per_step": best[1],
-                                     "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
-        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
-        with open(CACHE, "w") as fh:
-            json.dump(db, fh, indent=1)
+        _save(_key(dims, precision, families),
+              {"config": list(best[0]), "seconds_per_step": best[1], "steps": steps,
+               "table": [[list(c), t] for c, t in table], "when": time.strftime("%Y-%m-%dT%H:%M:%S")})
     return best[0], table
+
+
+def ensure_tuned(dims, precision, params, phi0, families=GENERAL, log=None):
+    """The cached choice for ``dims``/``precision``/``families``, tuning on
+    first use (the cache lives beside the built library)."""
+    hit = _load().get(_key(dims, precision, families))
+    if hit:
+        return tuple(hit["config"])
+    best, _ = autotune(dims, precision, params, phi0, families=families, log=log)
+    return tuple(best)
 
 
 def _batch_key(batch) -> str:

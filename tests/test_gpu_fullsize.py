@@ -28,10 +28,17 @@ def _setup():
     oracle.build()
 
 
-def _bench_lattice(params, precision):
-    from paper_1405_6162_gb300 import Lattice, tuning
+# the library's default step and the bulk-copy single pass (the kernels the
+# benchmark's autotuner chooses between at 256^3), in their default shapes
+KERNELS = ["auto", "bulk"]
+
+
+def _bench_lattice(params, precision, kernel="auto"):
+    from paper_1405_6162_gb300 import Lattice
+    if kernel == "bulk" and precision == "fp64_df":
+        pytest.skip("the bulk kernel takes FP64 and FP32-shifted storage")
     lat = Lattice.from_params(FULL, params, precision=precision)
-    lat.set_kernel(*tuning.bench_config(FULL, precision))
+    lat.set_kernel(kernel)
     return lat
 
 
@@ -58,14 +65,15 @@ def _tol(precision, name, nsteps):
     return TOL_FP64 if precision in ("fp64", "fp64_df") else TOL_FP32_1D_PER_STEP[name] * nsteps
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("precision", ["fp64", "fp32_shifted", "fp64_df"])
 @pytest.mark.parametrize("amplitude", [1.0, 0.5])
-def test_flat_interface_256cubed_equals_1d_oracle(precision, amplitude):
+def test_flat_interface_256cubed_equals_1d_oracle(precision, amplitude, kernel):
     nsteps = 40
     xi = L.interface_width(P0["A"], P0["kappa"])
     line = L.flat_interface_phi0(FULL[0], 1, 1, amplitude, xi)
     want, us = _one_d(P0, line, None, nsteps)
-    with _bench_lattice(P0, precision) as lat:
+    with _bench_lattice(P0, precision, kernel) as lat:
         lat.init(_broadcast(line))
         lat.step(nsteps)
         rho, u, phi = lat.moments()
@@ -78,14 +86,15 @@ def test_flat_interface_256cubed_equals_1d_oracle(precision, amplitude):
     assert np.abs(u[1:]).max() <= 1e-15
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("precision", ["fp64", "fp32_shifted", "fp64_df"])
 @pytest.mark.parametrize("tau", [0.6, 1.0])
-def test_shear_wave_256cubed_equals_1d_oracle(precision, tau):
+def test_shear_wave_256cubed_equals_1d_oracle(precision, tau, kernel):
     nsteps = 30
     p = dict(P0, tau=tau)
     u_line = L.shear_wave_u0(FULL[0], 1, 1, amp=0.01)
     want, us = _one_d(p, np.zeros(FULL[0]), u_line, nsteps)
-    with _bench_lattice(p, precision) as lat:
+    with _bench_lattice(p, precision, kernel) as lat:
         lat.init(np.zeros(int(np.prod(FULL))), np.stack([_broadcast(u_line[a]) for a in range(3)]))
         lat.step(nsteps)
         rho, u, phi = lat.moments()
@@ -102,16 +111,16 @@ def test_shear_wave_256cubed_equals_1d_oracle(precision, tau):
     assert np.abs(phi).max() == 0.0
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("precision", ["fp64", "fp32_shifted", "fp64_df"])
-def test_sampled_sites_one_step_256cubed(precision):
+def test_sampled_sites_one_step_256cubed(precision, kernel):
     import torch
-    from paper_1405_6162_gb300 import Lattice, tuning  # noqa: F401
     n = int(np.prod(FULL))
     nx, ny, nz = FULL
     phi0 = L.spinodal_phi0(*FULL, seed=90, amp=0.8)
     u0 = 0.02 * L.uniform(91, 3 * n, -1, 1).reshape(3, n)
     o2a = abi_order()
-    with _bench_lattice(P0, precision) as lat:
+    with _bench_lattice(P0, precision, kernel) as lat:
         lat.init(phi0, u0)
         lat.step(3)                                     # move away from equilibrium
         f0, g0 = lat.get_state(device=True)
