@@ -78,8 +78,11 @@ enum { LB_HOST = 0, LB_DEVICE = 1 };
 
 /* Step kernels selectable with lb_set_kernel(). */
 enum {
-    LB_KERNEL_AUTO = 0,     /* library default: the fastest measured on GB300
-                               at 256^3, currently LB_KERNEL_TWO_PASS          */
+    LB_KERNEL_AUTO = 0,     /* library default, the fastest measured on GB300:
+                               LB_KERNEL_BULK (3 slots, clusters of 2, 16
+                               planes) for FP32-shifted 7-point BGK steps on
+                               rows of 256 sites with ny even, else
+                               LB_KERNEL_TWO_PASS                            */
     LB_KERNEL_TWO_PASS = 1, /* phi pass + collide/stream pass (phi buffer)     */
     LB_KERNEL_FUSED = 2,    /* single pass, phi halo staged in shared memory   */
     LB_KERNEL_STAGED = 3,   /* single pass, planes staged by asynchronous
@@ -224,7 +227,8 @@ int lb_set_state_masked(lb_ctx *c, const unsigned char *mask, const double *f, c
  * LB_KERNEL_LAG block_x must be 0 or 256, block_y 0 or 1, and z_chunk is the
  * lag slack in site blocks beyond the stencil's reach (0 = default 128).
  * For LB_KERNEL_BULK block_x is the number of shared-memory plane slots of
- * g (3..8; 0 = 4 for FP32, 3 for FP64), block_y the CTAs per cluster along
+ * g (3..8, or 2 in FP32: the lean form, no copies ahead, three CTAs per SM;
+ * 0 = 3), block_y the CTAs per cluster along
  * y (1, 2, 4 or 8, dividing ny; 0 = 4) and z_chunk the planes each CTA
  * marches (0 = 32).
  * LB_KERNEL_TAUG1 requires tau_g == 1 (LB_ERR_INVALID otherwise) and

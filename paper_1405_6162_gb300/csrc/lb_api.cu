@@ -341,6 +341,7 @@ int lb_step(lb_ctx *c, int nsteps)
     if (!c || nsteps < 0 || c->batch_owned) return LB_ERR_INVALID;
     if (nsteps == 0) return LB_OK;
     if (c->reduced) return lbk::launch_step_taug1(c, nsteps);
+    if (c->kernel == LB_KERNEL_AUTO && lbk::auto_uses_bulk(c)) return lbk::launch_step_bulk_auto(c, nsteps);
     if (c->kernel == LB_KERNEL_TWO_PASS || c->kernel == LB_KERNEL_AUTO) return lbk::launch_step_two_pass(c, nsteps);
     if (c->kernel == LB_KERNEL_STAGED) return lbk::launch_step_staged(c, nsteps);
     if (c->kernel == LB_KERNEL_SLAB) return lbk::launch_step_slab(c, nsteps);

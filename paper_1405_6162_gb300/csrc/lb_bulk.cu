@@ -229,9 +229,10 @@ __host__ __device__ inline Smem smem_layout(int nx, int ng, int nsl, size_t esiz
 #endif
 
 // NXC: the row length as a compile-time constant (every shared-memory offset
-// an immediate), or 0 for any row length
-template <typename T, bool SH, int NXC>
-__global__ void __launch_bounds__(kBulkMaxRow, sizeof(T) == 4 ? LBK_BULK_MINB32 : 1)
+// an immediate), or 0 for any row length.  LEAN: two own-row slots (ng = 2)
+// and one local halo slot, refilled while the row collides; three CTAs per SM.
+template <typename T, bool SH, int NXC, bool LEAN>
+__global__ void __launch_bounds__(kBulkMaxRow, LEAN ? 3 : (sizeof(T) == 4 ? LBK_BULK_MINB32 : 1))
 k_bulk(const T *__restrict__ fa, const T *__restrict__ ga, T *__restrict__ fb, T *__restrict__ gb, Coll<T> p,
        BGeo G, unsigned int *err_flag)
 {
@@ -374,58 +375,110 @@ k_bulk(const T *__restrict__ fa, const T *__restrict__ ga, T *__restrict__ fb, T
         if (nloc == 2) halo[h * 2 * nx + nx + x] = sum_rows(base + (size_t)Q * nx);
     };
 
-    // prologue: groups 0 .. D + 1 in flight, phi of planes 0 and 1
-    load_f(z0);
-    for (int s = 0; s <= D + 1; s++) issue_group(s);
-    copies_wait_pending(D + 1);   // group 0
-    cta_sync_or(nct, false);
-    form_phi(0);
-    copies_wait_pending(D);       // group 1
-    cta_sync_or(nct, false);
-    form_phi(1);
+    // the g values of collision plane jc from its slot
+    auto load_g = [&](int jc, T (&g)[Q]) {
+        const T *gs = own + (size_t)(jc % G.ng) * Q * nx;
+#pragma unroll
+        for (int i = 0; i < Q; i++) g[i] = gs[i * nx + X[1 - cx(i)]];
+    };
+    // the collision of plane jc (index k = jc - 1 of the chunk) with its g
+    auto collide_row = [&](int k, T (&g)[Q]) {
+        const int jc = k + 1, jn = k + 2;
+        const int hc = (jc - 1) & (kRing - 1);
+        const T *pc = phir + (jc % kRing) * nx;
+        const T ph = pc[x];
+        const T xp = pc[X[2]], xm = pc[X[0]];
+        const T ym = halo[hc * 2 * nx + x], yp = halo[hc * 2 * nx + nx + x];
+        const T zp = phir[(jn % kRing) * nx + x], zm = phir[(k % kRing) * nx + x];
+        const T dx = T(0.5) * (xp - xm), dy = T(0.5) * (yp - ym), dz = T(0.5) * (zp - zm);
+        const T lap = ((xp + xm) + (yp + ym)) + (zp + zm) - T(6) * ph;
+        collide<T, SH>(p, fr, g, ph, dx, dy, dz, lap);
+        const size_t o = (size_t)(z0 + k) * plane + (size_t)y * nx + x;
+        T *pf = fb + o, *pg = gb + o;
+#pragma unroll
+        for (int i = 0; i < Q; i++, pf += G.S, pg += G.S) {
+            store(pf, fr[i]);
+            store(pg, g[i]);
+        }
+    };
+    // every thread has read the halo ring slot of plane k (collided in the
+    // previous iteration): arm it for plane k + 4
+    auto rearm = [&](int k) {
+        if (tid == 0 && k >= 1 && k + kRing <= ez) mbar_expect_tx(halo_full + 8 * ((k - 1) & (kRing - 1)), peer_bytes);
+    };
+    auto wait_halo = [&](int jc) {
+        if (npeer + G.stall == 0) return true;
+        return wait_peers(halo_full + 8 * ((jc - 1) & (kRing - 1)), (uint32_t)(((jc - 1) / kRing) & 1), G.timeout_ns,
+                          abort);
+    };
 
     bool ok = true;
-    for (int k = 0; k < ez; k++) {
-        const int jc = k + 1, jn = k + 2;   // collision plane, next phi plane
-        copies_wait_pending(D - 1);         // group jn: own rows of jn, local halo rows of jc
-        // the copies of group jn are visible CTA-wide, and every thread is
-        // past the previous collision, so the slots of plane k are free
-        if (cta_sync_or(nct, !ok || *abort)) break;
-        // every thread has read the halo ring slot of plane k (collided in
-        // the previous iteration): arm it for plane k + 4
-        if (tid == 0 && k >= 1 && k + kRing <= ez) mbar_expect_tx(halo_full + 8 * ((k - 1) & (kRing - 1)), peer_bytes);
-        issue_group(jn + D);
-        form_phi(jn);
-        form_local_halo(jc);
-        // No barrier here: the collision below reads, of what this iteration
-        // wrote, only the values at its own site (phi of jn, the local halo
-        // of jc); the x-neighbours' phi of jn are read in the next iteration,
-        // after its barrier, and the peers' halo rows through their barrier.
-        const int hc = (jc - 1) & (kRing - 1);
-        if (npeer + G.stall > 0)
-            ok = wait_peers(halo_full + 8 * hc, (uint32_t)(((jc - 1) / kRing) & 1), G.timeout_ns, abort);
-        if (ok && active) {
-            const T *gs = own + (size_t)(jc % G.ng) * Q * nx;
-            T g[Q];
-#pragma unroll
-            for (int i = 0; i < Q; i++) g[i] = gs[i * nx + X[1 - cx(i)]];
-            const T *pc = phir + (jc % kRing) * nx;
-            const T ph = pc[x];
-            const T xp = pc[X[2]], xm = pc[X[0]];
-            const T ym = halo[hc * 2 * nx + x], yp = halo[hc * 2 * nx + nx + x];
-            const T zp = phir[(jn % kRing) * nx + x], zm = phir[(k % kRing) * nx + x];
-            const T dx = T(0.5) * (xp - xm), dy = T(0.5) * (yp - ym), dz = T(0.5) * (zp - zm);
-            const T lap = ((xp + xm) + (yp + ym)) + (zp + zm) - T(6) * ph;
-            collide<T, SH>(p, fr, g, ph, dx, dy, dz, lap);
-            const size_t o = (size_t)(z0 + k) * plane + (size_t)y * nx + x;
-            T *pf = fb + o, *pg = gb + o;
-#pragma unroll
-            for (int i = 0; i < Q; i++, pf += G.S, pg += G.S) {
-                store(pf, fr[i]);
-                store(pg, g[i]);
+    if constexpr (!LEAN) {
+        // prologue: groups 0 .. D + 1 in flight, phi of planes 0 and 1
+        load_f(z0);
+        for (int s = 0; s <= D + 1; s++) issue_group(s);
+        copies_wait_pending(D + 1);   // group 0
+        cta_sync_or(nct, false);
+        form_phi(0);
+        copies_wait_pending(D);       // group 1
+        cta_sync_or(nct, false);
+        form_phi(1);
+        for (int k = 0; k < ez; k++) {
+            const int jc = k + 1, jn = k + 2;   // collision plane, next phi plane
+            copies_wait_pending(D - 1);         // group jn: own rows of jn, local halo rows of jc
+            // the copies of group jn are visible CTA-wide, and every thread is
+            // past the previous collision, so the slots of plane k are free
+            if (cta_sync_or(nct, !ok || *abort)) break;
+            rearm(k);
+            issue_group(jn + D);
+            form_phi(jn);
+            form_local_halo(jc);
+            // No barrier here: the collision below reads, of what this
+            // iteration wrote, only the values at its own site (phi of jn, the
+            // local halo of jc); the x-neighbours' phi of jn are read in the
+            // next iteration, after its barrier, and the peers' halo rows
+            // through their barrier.
+            ok = wait_halo(jc);
+            if (ok && active) {
+                T g[Q];
+                load_g(jc, g);
+                collide_row(k, g);
             }
+            if (k + 1 < ez) load_f(z0 + k + 1);
         }
-        if (k + 1 < ez) load_f(z0 + k + 1);
+    } else {
+        // Two own slots and one local halo slot, so that three CTAs fit an
+        // SM.  The slot of collision plane jc is free once every thread has
+        // its g values in registers: the copy of plane jc + 2 goes into it
+        // then and lands while the row collides.
+        issue_group(0);
+        copies_wait<0>();
+        cta_sync_or(nct, false);
+        form_phi(0);
+        issue_group(1);
+        copies_wait<0>();
+        cta_sync_or(nct, false);
+        form_phi(1);
+        issue_group(2);   // into plane 0's slot, whose phi is formed
+        for (int k = 0; k < ez; k++) {
+            const int jc = k + 1, jn = k + 2;
+            copies_wait<0>();   // group jn: own rows of jn, local halo rows of jc
+            // the copies of group jn are visible CTA-wide, every thread is
+            // past the previous collision
+            if (cta_sync_or(nct, !ok || *abort)) break;
+            rearm(k);
+            load_f(z0 + k);
+            form_phi(jn);
+            form_local_halo(jc);
+            ok = wait_halo(jc);
+            T g[Q];
+            load_g(jc, g);
+            // every thread has its g of jc and has formed the local halo of jc:
+            // jc's slot and the local halo slot take group jc + 2
+            cta_sync_or(nct, false);
+            issue_group(jc + 2);
+            if (ok && active) collide_row(k, g);
+        }
     }
     copies_drain();   // nothing in flight when the CTA exits
     if (tid == 0 && *abort) atomicExch(err_flag, 1u);
@@ -453,7 +506,7 @@ int bulk_validate(const lb_params &p, int block_x, int block_y, int z_chunk)
     if (p.precision != LB_FP64 && p.precision != LB_FP32_SHIFTED) return LB_ERR_INVALID;
     const size_t es = p.precision == LB_FP64 ? 8 : 4;
     if (p.nx > kBulkMaxRow || ((size_t)p.nx * es) % 16 != 0) return LB_ERR_INVALID;
-    if (ng < 3 || ng > 8) return LB_ERR_INVALID;
+    if (ng < 2 || ng > 8 || (ng == 2 && p.precision != LB_FP32_SHIFTED)) return LB_ERR_INVALID;
     if (cy != 1 && cy != 2 && cy != 4 && cy != 8) return LB_ERR_INVALID;
     if (p.ny % cy != 0) return LB_ERR_INVALID;
     if (zc < 1 || (p.nz + zc - 1) / zc > 65535) return LB_ERR_INVALID;
@@ -478,7 +531,10 @@ static int run_bulk(lb_ctx *c, int nsteps)
     G.timeout_ns = c->wait_timeout_ns;
     G.stall = c->lag_target_skew != 0;
     const size_t shm = bulk_smem_bytes(G.nx, G.ng, cy, sizeof(T));
-    auto kern = G.nx == 256 ? k_bulk<T, SH, 256> : k_bulk<T, SH, 0>;
+    // the lean form only in FP32 (validated), so only its FP32 copies exist
+    constexpr bool kLean = sizeof(T) == 4;
+    auto kern = (kLean && G.ng == 2) ? (G.nx == 256 ? k_bulk<T, SH, 256, kLean> : k_bulk<T, SH, 0, kLean>)
+                                     : (G.nx == 256 ? k_bulk<T, SH, 256, false> : k_bulk<T, SH, 0, false>);
     int rc = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     if (rc) return rc;
     const auto p = make_coll<T>(c->p);
@@ -503,6 +559,31 @@ static int run_bulk(lb_ctx *c, int nsteps)
         c->buf.cur = b;
     }
     return LB_OK;
+}
+
+// the shape the library default uses: 3 slots, clusters of 2, 16 planes per
+// CTA (the fastest measured at 256^3 FP32-shifted on GB300), on rows of 256
+// sites (eight warps a CTA; at 128^3, four warps a CTA, the two-pass step is
+// faster: 17.4 against 14.2 GLUPS)
+constexpr int kAutoSlots = 3, kAutoCluster = 2, kAutoPlanes = 16;
+
+bool auto_uses_bulk(const lb_ctx *c)
+{
+    return c->p.precision == LB_FP32_SHIFTED && c->npts == 7 && !uses_mrt(c) && c->p.nx == kBulkMaxRow &&
+           bulk_validate(c->p, kAutoSlots, kAutoCluster, kAutoPlanes) == LB_OK;
+}
+
+int launch_step_bulk_auto(lb_ctx *c, int nsteps)
+{
+    const int bx = c->block_x, by = c->block_y, zc = c->z_chunk;
+    c->block_x = kAutoSlots;
+    c->block_y = kAutoCluster;
+    c->z_chunk = kAutoPlanes;
+    const int rc = c->p.precision == LB_FP64 ? run_bulk<double, false>(c, nsteps) : run_bulk<float, true>(c, nsteps);
+    c->block_x = bx;
+    c->block_y = by;
+    c->z_chunk = zc;
+    return rc;
 }
 
 int launch_step_bulk(lb_ctx *c, int nsteps)

@@ -161,6 +161,10 @@ int lag_validate(int block_x, int block_y, int z_chunk);
 // bulk-copy single-pass kernel (lb_bulk.cu)
 int launch_step_bulk(lb_ctx *c, int nsteps);
 int bulk_validate(const lb_params &p, int block_x, int block_y, int z_chunk);
+// LB_KERNEL_AUTO: the bulk kernel in its fastest measured shape where it
+// applies (FP32-shifted, 7-point BGK, a shape it takes), else the two-pass step
+bool auto_uses_bulk(const lb_ctx *c);
+int launch_step_bulk_auto(lb_ctx *c, int nsteps);
 
 // slab kernel (lb_slab.cu)
 int launch_step_slab(lb_ctx *c, int nsteps);

@@ -87,7 +87,7 @@ def candidates(precision, dims=None, families=GENERAL, tau_g=None):
             for vvl in (1, 2, 4):
                 out.append(("two_pass", tpb, vvl, 0))
     if "bulk" in families and (dims is None or _bulk_ok(dims, precision)):
-        slots = (3, 4) if precision == "fp64" else (3, 4, 6)
+        slots = (3, 4) if precision == "fp64" else (2, 3, 4)
         for ng in slots:
             for cy in (1, 2, 4, 8):
                 if dims is not None and (dims[1] % cy or cy > dims[1]):

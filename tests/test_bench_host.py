@@ -53,6 +53,7 @@ def test_missing_summary_or_key():
 def test_committed_step_summaries_are_current():
     # the figures bench.py reports beside its timings come from these
     for name, key in (("step_fp32_shifted_256cubed", "dram_bytes_per_step"),
+                      ("step_bulk_fp32_shifted_256cubed", "dram_bytes_per_step"),
                       ("step_fp64_256cubed", "dram_bytes_per_step"),
                       ("step_fp64_256cubed", "fp64_instr_per_site"),
                       ("step_fp64_df_256cubed", "dram_bytes_per_step"),

@@ -28,9 +28,10 @@ def _setup():
     oracle.build()
 
 
-# the library's default step and the bulk-copy single pass (the kernels the
-# benchmark's autotuner chooses between at 256^3), in their default shapes
-KERNELS = ["auto", "bulk"]
+# the two-pass step, the bulk-copy single pass (the kernels the benchmark's
+# autotuner chooses between at 256^3, in their default shapes) and the
+# library default (the bulk kernel in FP32, the two-pass step in FP64)
+KERNELS = ["two_pass", "bulk", "auto"]
 
 
 def _bench_lattice(params, precision, kernel="auto"):
