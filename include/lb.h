@@ -233,7 +233,10 @@ int lb_set_state_masked(lb_ctx *c, const unsigned char *mask, const double *f, c
  * marches (0 = 32).
  * LB_KERNEL_TAUG1 requires tau_g == 1 (LB_ERR_INVALID otherwise) and
  * converts the stored state to its reduced form (selecting another kernel
- * converts back).  In that form lb_set_state keeps g only through
+ * converts back); its phi pass takes block_x y rows per warp (1, 2 or 4;
+ * 4 not in LB_FP64_DF; 0 = 1 in FP32, 2 otherwise), block_y warps per CTA
+ * (1..8; 0 = 4) and z_chunk planes per warp (0 = sized for about three
+ * waves of CTAs; cut to nz).  In that form lb_set_state keeps g only through
  * phi = sum_i g_i (all the tau_g = 1 dynamics uses) and lb_get_state reports
  * g as the streamed equilibria of the previous step (after lb_init or
  * lb_set_state: the equilibrium at each site).  Ensemble members refuse

@@ -410,7 +410,8 @@ int lb_set_kernel(lb_ctx *c, int kernel, int block_x, int block_y, int z_chunk)
         int rc = lbk::staged_validate(c->p.precision, block_x, block_y, z_chunk);
         if (rc) return rc;
     } else if (kernel == LB_KERNEL_TAUG1) {
-        if (c->p.tau_g != 1.0 || block_x || block_y || z_chunk) return LB_ERR_INVALID;
+        int rc = lbk::taug1_validate(c->p, block_x, block_y, z_chunk);
+        if (rc) return rc;
     } else if (kernel == LB_KERNEL_LAG) {
         int rc = lbk::lag_validate(block_x, block_y, z_chunk);
         if (rc) return rc;

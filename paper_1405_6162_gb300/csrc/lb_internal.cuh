@@ -142,6 +142,9 @@ int launch_adjoint_init(lb_ctx *c, const double *phi0, const double *u0, const d
 
 // tau_g = 1 reduced form (lb_taug1.cu)
 int launch_step_taug1(lb_ctx *c, int nsteps);
+// y rows per warp (0 = by precision; 1, 2, 4), warps per block (0 = 4; 1..8),
+// z run of the phi pass (0 = sized for about three waves)
+int taug1_validate(const lb_params &p, int block_x, int block_y, int z_chunk);
 int taug1_convert(lb_ctx *c, int to_reduced);
 int taug1_g_rows(lb_ctx *c, int i0, int i1, double *out);
 int taug1_phi_out(lb_ctx *c, double *out);

@@ -191,7 +191,7 @@ constexpr int kPhiOut = 30;    // output columns per warp
 #endif
 template <typename T>
 struct PhiTile {
-    // y rows per lane
+    // y rows per lane (the default launch; lb_set_kernel picks 1, 2 or 4)
     static constexpr int KY = is_df64<T>::value ? LBK_T1_KYDF : sizeof(T) == 8 ? LBK_T1_KY64 : LBK_T1_KY32;
 };
 
@@ -201,9 +201,22 @@ __device__ __forceinline__ int wrap_up(int v, int n)
     return v;
 }
 
+// raw moments (phi, gmh, u) of site o
+template <typename T>
+__device__ __forceinline__ void t1_load_site(const T *__restrict__ ga, const T *__restrict__ q0, int o, T (&d)[5])
+{
+    T v[4];
+    Quad<T>::load(q0, o, v);
+    d[0] = ga[o], d[1] = v[0], d[2] = v[1], d[3] = v[2], d[4] = v[3];
+}
+
 // The phi pass for the tile of one warp: x columns bx*30 - 1 .. bx*30 + 30
 // (lane = column - bx*30 + 1), y rows y0 .. y0 + KY - 1, output planes
-// bz*kzc .. bz*kzc + kzc - 1.  No block-level synchronisation.
+// bz*kzc .. bz*kzc + kzc - 1.  No block-level synchronisation.  Source plane
+// j of the run (z0 + j - 1, j = 0 .. nzc + 1) is summed row by row; once a
+// row's moments are expanded its registers take the same row of plane
+// j + 1, so a plane of arithmetic covers each load's latency and one plane
+// of raw moments is held.  Site offsets fit an int (N < 2^31).
 template <typename T, int KY>
 __device__ __forceinline__ void t1_phi_tile(const T *__restrict__ ga, T *__restrict__ gb, int nx, int ny, int nz,
                                             int kzc, long long S, int bx, int y0, int bz, int lane)
@@ -214,50 +227,35 @@ __device__ __forceinline__ void t1_phi_tile(const T *__restrict__ ga, T *__restr
     const int xu = bx * kPhiOut + lane - 1;   // unwrapped column, -1 .. nx + 30
     const int x = wrap_up(xu + nx, nx);
     const bool out_x = lane >= 1 && lane <= kPhiOut && xu < nx;
-    const long long plane = (long long)nx * ny;
+    const int plane = nx * ny;
     int yoff[KY + 2];
 #pragma unroll
-    for (int k = 0; k < KY + 2; k++) yoff[k] = wrap_up(y0 - 1 + k + ny, ny) * nx;
+    for (int k = 0; k < KY + 2; k++) yoff[k] = x + wrap_up(y0 - 1 + k + ny, ny) * nx;
     // partial sums of output plane oz live in slot oz mod 3
     T acc[3][KY], acc_r[3][KY], acc_l[3][KY];
 #pragma unroll
     for (int q = 0; q < 3; q++)
 #pragma unroll
         for (int a = 0; a < KY; a++) acc[q][a] = acc_r[q][a] = acc_l[q][a] = T(0);
-    // raw moments of the next source plane, loaded one plane ahead
-    int zr = wrap_up(z0 - 1 + nz, nz);   // source plane of step j: z0 + j - 1
     const T *q0 = quads(ga, S);
-    T nxt[KY + 2][5];
+    T raw[KY + 2][5];
+    // source plane 0 of the run
+    int zl = wrap_up(z0 - 1 + nz, nz) * plane;   // offset of the next plane to load
 #pragma unroll
-    for (int r = 0; r < KY + 2; r++) {
-        const long long o = x + zr * plane + yoff[r];
-        T v[4];
-        Quad<T>::load(q0, o, v);
-        nxt[r][0] = ga[o], nxt[r][1] = v[0], nxt[r][2] = v[1], nxt[r][3] = v[2], nxt[r][4] = v[3];
-    }
+    for (int r = 0; r < KY + 2; r++) t1_load_site(ga, q0, zl + yoff[r], raw[r]);
+    zl += plane;
+    if (zl == plane * nz) zl = 0;
     for (int j0 = 0; j0 < nzc + 2; j0 += 3) {
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             const int j = j0 + k;
             if (j >= nzc + 2) break;   // uniform over the warp
-            T cur[KY + 2][5];
-#pragma unroll
-            for (int r = 0; r < KY + 2; r++)
-#pragma unroll
-                for (int m = 0; m < 5; m++) cur[r][m] = nxt[r][m];
-            zr = zr + 1 == nz ? 0 : zr + 1;
-            const long long zo = zr * plane;   // one plane past the last is still in range
-#pragma unroll
-            for (int r = 0; r < KY + 2; r++) {
-                const long long o = x + zo + yoff[r];
-                T v[4];
-                Quad<T>::load(q0, o, v);
-                nxt[r][0] = ga[o], nxt[r][1] = v[0], nxt[r][2] = v[1], nxt[r][3] = v[2], nxt[r][4] = v[3];
-            }
+            const bool more = j + 1 < nzc + 2;   // uniform: plane j + 1 is part of the run
 #pragma unroll
             for (int ry = -1; ry <= KY; ry++) {
-                const T *c5 = cur[ry + 1];
+                T (&c5)[5] = raw[ry + 1];
                 const Eq<T> e = make_eq(c5[0], c5[1], c5[2], c5[3], c5[4]);
+                if (more) t1_load_site(ga, q0, zl + yoff[ry + 1], c5);
 #pragma unroll
                 for (int i = 0; i < Q; i++) {
                     const int oy = ry + cy(i);
@@ -272,6 +270,10 @@ __device__ __forceinline__ void t1_phi_tile(const T *__restrict__ ga, T *__restr
                         acc_l[q][oy] += v;   // to column x - 1
                 }
             }
+            if (more) {
+                zl += plane;
+                if (zl == plane * nz) zl = 0;
+            }
             // output plane j - 2 (slot (k + 1) mod 3) is complete
             const int qd = (k + 1) % 3;
             const int oz = j - 2;
@@ -280,7 +282,7 @@ __device__ __forceinline__ void t1_phi_tile(const T *__restrict__ ga, T *__restr
                 const T from_left = shfl_up1(acc_r[qd][a]);
                 const T from_right = shfl_down1(acc_l[qd][a]);
                 if (out_x && oz >= 0 && y0 + a < ny)
-                    gb[x + yoff[a + 1] + (z0 + oz) * plane] = acc[qd][a] + (from_left + from_right);
+                    gb[yoff[a + 1] + (z0 + oz) * plane] = acc[qd][a] + (from_left + from_right);
                 acc[qd][a] = acc_r[qd][a] = acc_l[qd][a] = T(0);
             }
         }

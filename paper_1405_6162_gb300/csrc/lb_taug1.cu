@@ -59,14 +59,15 @@ k_t1_collide(const T *__restrict__ fa, T *__restrict__ ga /* level a: phi in, (g
     t1_collide_site<T, SH, NP>(fa, ga, fb, p, nx, ny, nz, S, s);
 }
 
-constexpr int kPhiWarps = 4;   // warps per block, stacked in y
+constexpr int kPhiWarps = 4;      // default warps per block, stacked in y
+constexpr int kPhiMaxWarps = 8;
 
 template <typename T, int KY>
-__global__ void __launch_bounds__(32 * kPhiWarps) k_t1_phi(const T *__restrict__ ga, T *__restrict__ gb, int nx,
-                                                            int ny, int nz, int kzc, long long S)
+__global__ void __launch_bounds__(32 * kPhiMaxWarps) k_t1_phi(const T *__restrict__ ga, T *__restrict__ gb, int nx,
+                                                               int ny, int nz, int kzc, long long S)
 {
     pdl_wait_then_release();
-    t1_phi_tile<T, KY>(ga, gb, nx, ny, nz, kzc, S, blockIdx.x, (blockIdx.y * kPhiWarps + threadIdx.y) * KY,
+    t1_phi_tile<T, KY>(ga, gb, nx, ny, nz, kzc, S, blockIdx.x, (blockIdx.y * blockDim.y + threadIdx.y) * KY,
                        blockIdx.z, threadIdx.x);
 }
 
@@ -164,35 +165,53 @@ __global__ void __launch_bounds__(kT1Threads) k_t1_copy_phi(const T *__restrict_
 
 inline unsigned grid_of(long long N) { return (unsigned)((N + kT1Threads - 1) / kT1Threads); }
 
-template <typename T, bool SH, int NP>
+// resident CTAs per SM of a phi-pass kernel and block size
+template <typename K>
+int blocks_per_sm(K kernel, int threads, int smem, std::atomic<int> &cache, int *bps)
+{
+    int b = cache.load(std::memory_order_relaxed);
+    if (!b) {
+        const int rc = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem));
+        if (rc) return rc;
+        b = b > 0 ? b : 1;
+        cache.store(b, std::memory_order_relaxed);
+    }
+    *bps = b;
+    return LB_OK;
+}
+
+// z run of the phi pass: the launch's choice, else 8..64 planes, as long as
+// about three waves of resident blocks remain
+int phi_z_run(lb_ctx *c, long long columns, int bps, int *kzc)
+{
+    int z = c->z_chunk;
+    if (!z) {
+        int dev = 0, sms = 0;
+        int rc = cuda_status(cudaGetDevice(&dev));
+        if (!rc) rc = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (rc) return rc;
+        const long long want = 3LL * sms * bps;
+        const long long zz = (long long)c->p.nz * columns / (want > 0 ? want : 1);
+        z = zz < 8 ? 8 : (zz > 64 ? 64 : (int)zz);
+    }
+    *kzc = z > c->p.nz ? c->p.nz : z;
+    return LB_OK;
+}
+
+template <typename T, bool SH, int NP, int KY>
 int run_t1(lb_ctx *c, int nsteps)
 {
     const auto p = make_coll<T>(c->p);
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
     const unsigned grid = grid_of(c->N);
-    constexpr int KY = PhiTile<T>::KY;
-    const unsigned gx = (nx + kPhiOut - 1) / kPhiOut, gy = (ny + KY * kPhiWarps - 1) / (KY * kPhiWarps);
-    // z runs of 8..64 planes: as long as about three waves of resident blocks remain
-    static std::atomic<int> bps_cache{0};   // per instantiation: resident phi-pass CTAs per SM
-    int bps = bps_cache.load(std::memory_order_relaxed);
-    if (!bps) {
-        int b = 0;
-        const int rc1 = cuda_status(
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_t1_phi<T, KY>, 32 * kPhiWarps, 0));
-        if (rc1) return rc1;
-        bps = b > 0 ? b : 1;
-        bps_cache.store(bps, std::memory_order_relaxed);
-    }
-    int dev = 0, sms = 0;
-    int rc0 = cuda_status(cudaGetDevice(&dev));
-    if (!rc0) rc0 = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (rc0) return rc0;
-    const long long want = 3LL * sms * bps;
-    int kzc = (int)((long long)nz * gx * gy / (want > 0 ? want : 1));
-    kzc = kzc < 8 ? 8 : (kzc > 64 ? 64 : kzc);
-    if (kzc > nz) kzc = nz;
-    const dim3 pgrid(gx, gy, (nz + kzc - 1) / kzc);
-    const dim3 pblock(32, kPhiWarps);
+    const int warps = c->block_y ? c->block_y : kPhiWarps;
+    const unsigned gx = (nx + kPhiOut - 1) / kPhiOut, gy = (ny + KY * warps - 1) / (KY * warps);
+    static std::atomic<int> cache[kPhiMaxWarps + 1];
+    int bps = 0, kzc = 0;
+    int rc = blocks_per_sm(k_t1_phi<T, KY>, 32 * warps, 0, cache[warps], &bps);
+    if (!rc) rc = phi_z_run(c, (long long)gx * gy, bps, &kzc);
+    if (rc) return rc;
+    const dim3 pgrid(gx, gy, (nz + kzc - 1) / kzc), pblock(32, warps);
     for (int t = 0; t < nsteps; t++) {
         const int a = c->buf.cur, b = 1 - a;
         cudaError_t e = launch_pdl(k_t1_collide<T, SH, NP>, grid, kT1Threads, c->stream, (const T *)c->buf.f[a],
@@ -200,7 +219,7 @@ int run_t1(lb_ctx *c, int nsteps)
         if (e == cudaSuccess)
             e = launch_pdl(k_t1_phi<T, KY>, pgrid, pblock, c->stream, (const T *)c->buf.g[a], (T *)c->buf.g[b], nx,
                            ny, nz, kzc, c->S);
-        const int rc = e != cudaSuccess ? cuda_status(e) : check_launch();
+        rc = e != cudaSuccess ? cuda_status(e) : check_launch();
         if (rc) return rc;
         c->buf.cur = b;
         c->m_valid = 1;
@@ -208,14 +227,27 @@ int run_t1(lb_ctx *c, int nsteps)
     return LB_OK;
 }
 
+template <typename T, bool SH, int NP>
+int run_t1_ky(lb_ctx *c, int nsteps)
+{
+    switch (c->block_x ? c->block_x : PhiTile<T>::KY) {
+    case 1: return run_t1<T, SH, NP, 1>(c, nsteps);
+    case 2: return run_t1<T, SH, NP, 2>(c, nsteps);
+    case 4:
+        if constexpr (is_df64<T>::value) return LB_ERR_INVALID;   // spills at four rows
+        else return run_t1<T, SH, NP, 4>(c, nsteps);
+    default: return LB_ERR_INVALID;
+    }
+}
+
 }  // namespace
 
 template <typename T, bool SH>
 int run_t1_t(lb_ctx *c, int nsteps)
 {
-    if (c->npts == 19) return run_t1<T, SH, 19>(c, nsteps);
-    if (c->npts == 27) return run_t1<T, SH, 27>(c, nsteps);
-    return run_t1<T, SH, 7>(c, nsteps);
+    if (c->npts == 19) return run_t1_ky<T, SH, 19>(c, nsteps);
+    if (c->npts == 27) return run_t1_ky<T, SH, 27>(c, nsteps);
+    return run_t1_ky<T, SH, 7>(c, nsteps);
 }
 
 template <typename T, bool SH, int NP>
@@ -224,8 +256,8 @@ void to_full(lb_ctx *c)
     const int cur = c->buf.cur, oth = 1 - cur;
     k_t1_copy_phi<T><<<grid_of(c->N), kT1Threads, 0, c->stream>>>((const T *)c->buf.g[cur], (T *)c->phi, c->N);
     k_t1_to_full<T, SH, NP><<<grid_of(c->N), kT1Threads, 0, c->stream>>>(
-        (const T *)c->buf.f[cur], (const T *)c->phi, (const T *)c->buf.g[oth], c->m_valid, make_coll<T>(c->p),
-        (T *)c->buf.g[cur], c->p.nx, c->p.ny, c->p.nz, c->S);
+        (const T *)c->buf.f[cur], (const T *)c->phi, (const T *)c->buf.g[oth], c->m_valid,
+        make_coll<T>(c->p), (T *)c->buf.g[cur], c->p.nx, c->p.ny, c->p.nz, c->S);
 }
 
 template <typename T, bool SH>
@@ -257,6 +289,15 @@ void g_rows_t(lb_ctx *c, int i0, int i1, double *out)
         g_rows<T, SH, 27>(c, i0, i1, out);
     else
         g_rows<T, SH, 7>(c, i0, i1, out);
+}
+
+int taug1_validate(const lb_params &p, int block_x, int block_y, int z_chunk)
+{
+    if (p.tau_g != 1.0) return LB_ERR_INVALID;
+    if (block_x != 0 && block_x != 1 && block_x != 2 && block_x != 4) return LB_ERR_INVALID;
+    if (block_x == 4 && p.precision == LB_FP64_DF) return LB_ERR_INVALID;
+    if (block_y < 0 || block_y > kPhiMaxWarps || z_chunk < 0) return LB_ERR_INVALID;
+    return LB_OK;
 }
 
 int launch_step_taug1(lb_ctx *c, int nsteps)

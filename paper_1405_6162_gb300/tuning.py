@@ -12,7 +12,8 @@ lattice, among the step kernels themselves and their launch shapes:
   CTA of the bulk-copy single pass, ``("bulk", slots, cluster, z_chunk)``;
 * ``fused``: CTA tile and z run of the shared-memory fused kernel;
 * ``taug1``: the tau_g = 1 reduced form, only when tau_g = 1 and asked for
-  (it keeps a different state, so it is a separate family).
+  (it keeps a different state, so it is a separate family): y rows per warp,
+  warps per CTA and z run of its phi pass, ``("taug1", rows, warps, z_run)``.
 
 ``autotune`` times every candidate on the GPU through the C ABI and keeps the
 fastest in an on-disk cache keyed by GPU name, lattice extents, precision
@@ -41,7 +42,7 @@ def _gpu_name() -> str:
 
 
 def _key(dims, precision, families=GENERAL) -> str:
-    return f"{_gpu_name()}|{dims[0]}x{dims[1]}x{dims[2]}|{precision}|{'+'.join(families)}|v2"
+    return f"{_gpu_name()}|{dims[0]}x{dims[1]}x{dims[2]}|{precision}|{'+'.join(families)}|v3"
 
 
 def _load() -> dict:
@@ -98,7 +99,11 @@ def candidates(precision, dims=None, families=GENERAL, tau_g=None):
         for bx, by, zc in ((32, 4, 32), (64, 2, 32), (32, 8, 64), (64, 4, 16)):
             out.append(("fused", bx, by, zc))
     if "taug1" in families and tau_g == 1.0:
-        out.append(("taug1", 0, 0, 0))
+        # the phi pass's y rows per warp, warps per CTA and z run
+        for ky in (1, 2) if precision == "fp64_df" else (1, 2, 4):
+            for warps in (4, 8):
+                for zc in (0, 32, 64):
+                    out.append(("taug1", ky, warps, zc))
     return out
 
 

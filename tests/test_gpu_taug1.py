@@ -134,3 +134,84 @@ def test_reduced_form_256cubed_flat_interface_equals_1d_oracle(precision):
         assert e_phi <= tol and e_rho <= tol
     else:
         assert e_phi <= TOL_FP32_PER_STEP["phi"] * nsteps and e_rho <= TOL_FP32_PER_STEP["rho"] * nsteps
+
+
+# phi-pass launch shapes (y rows per warp, warps per block, z run): one, two
+# and four rows per lane (FP32: the even ones as paired FP32 arithmetic on row
+# pairs), ragged y (an odd last row pair), several z runs with a ragged last
+# one, and runs longer than nz
+PHI_SHAPES = [(1, 4, 0), (2, 4, 0), (4, 8, 64), (2, 1, 3), (4, 2, 5), (2, 8, 7)]
+
+
+@pytest.mark.parametrize("shape", PHI_SHAPES)
+@pytest.mark.parametrize("dims", [(40, 9, 35), (70, 37, 11), (13, 7, 5)])
+def test_phi_pass_shapes_fp64(dims, shape):
+    p = dict(P0, tau=0.8)
+    phi0 = L.spinodal_phi0(*dims, seed=350, amp=0.4)
+    fo, go = oracle.step(dims, p, *oracle.init(dims, p, phi0), 6)
+    from paper_1405_6162_gb300 import Lattice
+    with Lattice.from_params(dims, p, precision="fp64") as lat:
+        lat.set_kernel("taug1", *shape)
+        lat.init(phi0)
+        lat.step(6)
+        _check(lat.moments(), oracle.moments(dims, fo, go), TOL_FP64, fo)
+        f, g = lat.get_state()
+    assert rel(to_oracle(g), go) <= TOL_FP64
+
+
+@pytest.mark.parametrize("shape", PHI_SHAPES)
+@pytest.mark.parametrize("dims", [(40, 9, 35), (70, 37, 11), (32, 32, 32),
+                                  (64, 9, 35), (128, 7, 11), (192, 5, 6), (1024, 3, 4)])
+def test_phi_pass_shapes_fp32_shifted(dims, shape):
+    """FP32 at the per-step bounds of the default shape, and within a few
+    FP32 roundings per step of the default shape's phi."""
+    phi0 = L.spinodal_phi0(*dims, seed=360, amp=0.3)
+    nsteps = 10
+    fo, go = oracle.step(dims, P0, *oracle.init(dims, P0, phi0), nsteps)
+    from paper_1405_6162_gb300 import Lattice
+    out = []
+    for s in ((0, 0, 0), shape):
+        with Lattice.from_params(dims, P0, precision="fp32_shifted") as lat:
+            lat.set_kernel("taug1", *s)
+            lat.init(phi0)
+            lat.step(nsteps)
+            out.append(lat.moments())
+    _check(out[1], oracle.moments(dims, fo, go), {k: v * nsteps for k, v in TOL_FP32_PER_STEP.items()}, fo)
+    assert np.abs(out[1][2] - out[0][2]).max() <= 8 * nsteps * 2.0 ** -24 * np.abs(out[0][2]).max()
+
+
+def test_phi_pass_shape_refusals():
+    from paper_1405_6162_gb300 import LBError, Lattice
+    with Lattice.from_params((16, 8, 8), P0, precision="fp64_df") as lat:
+        with pytest.raises(LBError):
+            lat.set_kernel("taug1", 4, 0, 0)      # four rows per lane spill in double-float
+    with Lattice.from_params((16, 8, 8), P0, precision="fp32_shifted") as lat:
+        for bad in ((3, 0, 0), (8, 0, 0), (0, 9, 0)):
+            with pytest.raises(LBError):
+                lat.set_kernel("taug1", *bad)
+        lat.set_kernel("taug1", 4, 8, 100)     # a z run longer than nz is cut to nz
+        lat.init(np.zeros(16 * 8 * 8))
+        lat.step(2)
+        lat.sync()
+
+
+@pytest.mark.parametrize("dims", [(64, 6, 5), (128, 3, 7)])
+def test_reduced_state_and_form_switches_fp32(dims):
+    """FP32: the g rebuilt from the stored moments matches the oracle's g, and
+    switching to the general form and back (which rebuilds g from them) keeps
+    the trajectory."""
+    phi0 = L.spinodal_phi0(*dims, seed=370, amp=0.3)
+    fo, go = oracle.step(dims, P0, *oracle.init(dims, P0, phi0), 3)
+    f9, g9 = oracle.step(dims, P0, *oracle.init(dims, P0, phi0), 9)
+    tol_g = 3 * 4e-7
+    with _lat(dims, P0, "fp32_shifted") as lat:
+        lat.init(phi0)
+        lat.step(3)
+        f, g = lat.get_state()
+        assert rel(to_oracle(g), go) <= tol_g
+        lat.set_kernel("two_pass")
+        lat.step(3)
+        lat.set_kernel("taug1")
+        lat.step(3)
+        got = lat.moments()
+    _check(got, oracle.moments(dims, f9, g9), {k: v * 9 for k, v in TOL_FP32_PER_STEP.items()}, f9)
