@@ -52,6 +52,9 @@ namespace {
 #ifndef LBK_BATCH_MINB32_RED
 #define LBK_BATCH_MINB32_RED 4
 #endif
+#ifndef LBK_BATCH_PHI_V
+#define LBK_BATCH_PHI_V 2
+#endif
 #ifndef LBK_BATCH_MINB64
 #define LBK_BATCH_MINB64 2
 #endif
@@ -70,6 +73,7 @@ struct LatDesc {
 };
 
 constexpr int kBatchT1Kzc = 8;   // z run of a reduced-form phi tile in the ensemble
+constexpr int kBatchPhiV = LBK_BATCH_PHI_V;   // phi-pass work items per trip (general form)
 
 struct GridBarrier {
     unsigned int count;
@@ -166,13 +170,21 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kBatchMaxThreads64 : kBatchMa
     } else {
         for (int t = 0; t < nsteps; t++) {
             const int a = (parity0 + t) & 1;
-            for (int w = G.wo + r; w < wend; w += G.m) {
-                const int2 it = work[w];
-                const LatDesc<T> &L = lats[it.x];
-                const long long s = (long long)it.y * blockDim.x + threadIdx.x;
-                if (s < L.N) {
-                    const Nbr n((int)s, L.nx, L.ny, L.nz);
-                    L.phi[s] = phi_site(L.g[a], n, L.S);
+            // kBatchPhiV work items per trip, their loads independent, so that
+            // the phi pass keeps as many loads in flight as its own kernel
+            // would at full occupancy (the collide pass sets the residency)
+            for (int w0 = G.wo + r; w0 < wend; w0 += kBatchPhiV * G.m) {
+#pragma unroll
+                for (int u = 0; u < kBatchPhiV; u++) {
+                    const int w = w0 + u * G.m;
+                    if (w >= wend) break;
+                    const int2 it = work[w];
+                    const LatDesc<T> &L = lats[it.x];
+                    const long long s = (long long)it.y * blockDim.x + threadIdx.x;
+                    if (s < L.N) {
+                        const Nbr n((int)s, L.nx, L.ny, L.nz);
+                        L.phi[s] = phi_site(L.g[a], n, L.S);
+                    }
                 }
             }
             if ((int)blockIdx.x == skip_cta) return;   // test hook: this CTA never arrives
