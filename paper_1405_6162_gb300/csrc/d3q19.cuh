@@ -28,6 +28,13 @@ __device__ __forceinline__ T fmadd(T a, T b, T c)
     return a * b + c;
 }
 
+// a * b + (c + d); for df64 one fused form (df64.cuh) that renormalises once
+template <typename T>
+__device__ __forceinline__ T fmadd_sum(T a, T b, T c, T d)
+{
+    return fmadd(a, b, c + d);
+}
+
 template <typename T>
 __device__ __forceinline__ void store(T *p, T v)
 {
@@ -194,8 +201,8 @@ __device__ __forceinline__ void collide_f(const Coll<T>& p, T (&f)[Q], T phi, T 
 #define LBK_FACE(IP, IM, SAA, JA)                                  \
     {                                                              \
         const T s_ = fmadd(p.f1h, SAA, B1), a_ = p.f1t * JA;       \
-        f[IP] = fmadd(cf, f[IP], s_ + a_);                         \
-        f[IM] = fmadd(cf, f[IM], s_ - a_);                         \
+        f[IP] = fmadd_sum(cf, f[IP], s_, a_);                      \
+        f[IM] = fmadd_sum(cf, f[IM], s_, -a_);                     \
     }
     LBK_FACE(1, 2, Sxx, jx)
     LBK_FACE(3, 4, Syy, jy)
@@ -207,10 +214,10 @@ __device__ __forceinline__ void collide_f(const Coll<T>& p, T (&f)[Q], T phi, T 
         const T e_ = fmadd(p.f2h, SAA + SBB, B2), o_ = p.f1h * SAB;  \
         const T sp = e_ + o_, sm = e_ - o_;                          \
         const T ap = p.f2t * (JA + JB), am = p.f2t * (JA - JB);      \
-        f[IP] = fmadd(cf, f[IP], sp + ap);                           \
-        f[IM] = fmadd(cf, f[IM], sp - ap);                           \
-        f[KP] = fmadd(cf, f[KP], sm + am);                           \
-        f[KM] = fmadd(cf, f[KM], sm - am);                           \
+        f[IP] = fmadd_sum(cf, f[IP], sp, ap);                        \
+        f[IM] = fmadd_sum(cf, f[IM], sp, -ap);                       \
+        f[KP] = fmadd_sum(cf, f[KP], sm, am);                        \
+        f[KM] = fmadd_sum(cf, f[KM], sm, -am);                       \
     }
     LBK_EDGES(7, 8, 9, 10, Sxx, Syy, Sxy, jx, jy)
     LBK_EDGES(11, 12, 13, 14, Sxx, Szz, Sxz, jx, jz)
@@ -235,8 +242,8 @@ __device__ __forceinline__ void collide_g(const Coll<T>& p, T (&g)[Q], T phi, T 
 #define LBK_GFACE(IP, IM, PA, UA)                                   \
     {                                                               \
         const T s_ = fmadd(p.g1h, PA * UA, G1), a_ = p.g1t * PA;    \
-        g[IP] = fmadd(cg, g[IP], s_ + a_);                          \
-        g[IM] = fmadd(cg, g[IM], s_ - a_);                          \
+        g[IP] = fmadd_sum(cg, g[IP], s_, a_);                       \
+        g[IM] = fmadd_sum(cg, g[IM], s_, -a_);                      \
     }
     LBK_GFACE(1, 2, px, ux)
     LBK_GFACE(3, 4, py, uy)
@@ -246,8 +253,8 @@ __device__ __forceinline__ void collide_g(const Coll<T>& p, T (&g)[Q], T phi, T 
     {                                                               \
         const T pc_ = PC, cu_ = CU;                                 \
         const T s_ = fmadd(p.g2h, pc_ * cu_, G2), a_ = p.g2t * pc_; \
-        g[IP] = fmadd(cg, g[IP], s_ + a_);                          \
-        g[IM] = fmadd(cg, g[IM], s_ - a_);                          \
+        g[IP] = fmadd_sum(cg, g[IP], s_, a_);                       \
+        g[IM] = fmadd_sum(cg, g[IM], s_, -a_);                      \
     }
     LBK_GEDGE(7, 8, px + py, ux + uy)
     LBK_GEDGE(9, 10, px - py, ux - uy)
