@@ -59,7 +59,11 @@ def to_oracle(x):
 def gpu_lattice(dims, params, precision="fp64", kernel="auto", block=(0, 0, 0)):
     from paper_1405_6162_gb300 import Lattice
     lat = Lattice.from_params(dims, params, precision=precision)
-    lat.set_kernel(kernel, *block)
+    try:
+        lat.set_kernel(kernel, *block)
+    except Exception:
+        lat.close()
+        raise
     return lat
 
 

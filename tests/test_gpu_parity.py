@@ -20,7 +20,8 @@ KERNEL_CASES = [("two_pass", (0, 0, 0)), ("fused", (0, 0, 0)), ("fused", (64, 2,
                 ("fused", (32, 1, 1)), ("fused", (128, 2, 7)), ("staged", (0, 0, 0)),
                 ("staged", (64, 2, 5)), ("staged", (32, 1, 1)), ("staged", (32, 4, 3)),
                 ("slab", (0, 0, 0)), ("slab", (64, 2, 5)), ("slab", (32, 1, 1)), ("slab", (128, 2, 3)),
-                ("lag", (0, 0, 0)), ("lag", (256, 1, 1))]
+                ("lag", (0, 0, 0)), ("lag", (256, 1, 1)),
+                ("bulk", (0, 0, 0)), ("bulk", (4, 8, 7)), ("bulk", (3, 1, 32))]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -68,10 +69,19 @@ RAGGED = [(13, 7, 5), (1, 1, 9), (33, 1, 2), (5, 17, 1), (40, 9, 35), (1, 1, 1),
 @pytest.mark.parametrize("dims", RAGGED)
 @pytest.mark.parametrize("kernel,block", KERNEL_CASES)
 def test_ragged_nonequilibrium_fp64(dims, kernel, block):
+    from paper_1405_6162_gb300 import LBError
     p = dict(P0, tau=0.7, tau_g=0.9, kappa=0.06)
     f0, g0 = nonequilibrium_state(dims, p, seed=31)
     (fo, go), mo = _oracle_run(dims, p, f0, g0, 4)
-    with gpu_lattice(dims, p, "fp64", kernel, block) as lat:
+    try:
+        lat = gpu_lattice(dims, p, "fp64", kernel, block)
+    except LBError:
+        if kernel != "bulk":
+            raise
+        # rows that are not whole 16-byte units, or ny not a multiple of the
+        # cluster: refused (test_gpu_bulk checks the refusals)
+        pytest.skip("shape outside the bulk kernel's limits")
+    with lat:
         lat.set_state(to_abi(f0), to_abi(g0))
         lat.step(4)
         _check_moments(lat.moments(), mo, TOL_FP64, fo)
