@@ -35,6 +35,15 @@ __device__ __forceinline__ T fmadd_sum(T a, T b, T c, T d)
     return fmadd(a, b, c + d);
 }
 
+// the relaxation of an opposite pair: fp = c fp + (s + a), fm = c fm + (s - a);
+// for df64 one pass of paired FP32 instructions over both (df64.cuh)
+template <typename T>
+__device__ __forceinline__ void relax_pair(T c, T &fp, T &fm, T s, T a)
+{
+    fp = fmadd_sum(c, fp, s, a);
+    fm = fmadd_sum(c, fm, s, -a);
+}
+
 template <typename T>
 __device__ __forceinline__ void store(T *p, T v)
 {
@@ -201,8 +210,7 @@ __device__ __forceinline__ void collide_f(const Coll<T>& p, T (&f)[Q], T phi, T 
 #define LBK_FACE(IP, IM, SAA, JA)                                  \
     {                                                              \
         const T s_ = fmadd(p.f1h, SAA, B1), a_ = p.f1t * JA;       \
-        f[IP] = fmadd_sum(cf, f[IP], s_, a_);                      \
-        f[IM] = fmadd_sum(cf, f[IM], s_, -a_);                     \
+        relax_pair(cf, f[IP], f[IM], s_, a_);                      \
     }
     LBK_FACE(1, 2, Sxx, jx)
     LBK_FACE(3, 4, Syy, jy)
@@ -214,10 +222,8 @@ __device__ __forceinline__ void collide_f(const Coll<T>& p, T (&f)[Q], T phi, T 
         const T e_ = fmadd(p.f2h, SAA + SBB, B2), o_ = p.f1h * SAB;  \
         const T sp = e_ + o_, sm = e_ - o_;                          \
         const T ap = p.f2t * (JA + JB), am = p.f2t * (JA - JB);      \
-        f[IP] = fmadd_sum(cf, f[IP], sp, ap);                        \
-        f[IM] = fmadd_sum(cf, f[IM], sp, -ap);                       \
-        f[KP] = fmadd_sum(cf, f[KP], sm, am);                        \
-        f[KM] = fmadd_sum(cf, f[KM], sm, -am);                       \
+        relax_pair(cf, f[IP], f[IM], sp, ap);                        \
+        relax_pair(cf, f[KP], f[KM], sm, am);                        \
     }
     LBK_EDGES(7, 8, 9, 10, Sxx, Syy, Sxy, jx, jy)
     LBK_EDGES(11, 12, 13, 14, Sxx, Szz, Sxz, jx, jz)
@@ -242,8 +248,7 @@ __device__ __forceinline__ void collide_g(const Coll<T>& p, T (&g)[Q], T phi, T 
 #define LBK_GFACE(IP, IM, PA, UA)                                   \
     {                                                               \
         const T s_ = fmadd(p.g1h, PA * UA, G1), a_ = p.g1t * PA;    \
-        g[IP] = fmadd_sum(cg, g[IP], s_, a_);                       \
-        g[IM] = fmadd_sum(cg, g[IM], s_, -a_);                      \
+        relax_pair(cg, g[IP], g[IM], s_, a_);                       \
     }
     LBK_GFACE(1, 2, px, ux)
     LBK_GFACE(3, 4, py, uy)
@@ -253,8 +258,7 @@ __device__ __forceinline__ void collide_g(const Coll<T>& p, T (&g)[Q], T phi, T 
     {                                                               \
         const T pc_ = PC, cu_ = CU;                                 \
         const T s_ = fmadd(p.g2h, pc_ * cu_, G2), a_ = p.g2t * pc_; \
-        g[IP] = fmadd_sum(cg, g[IP], s_, a_);                       \
-        g[IM] = fmadd_sum(cg, g[IM], s_, -a_);                      \
+        relax_pair(cg, g[IP], g[IM], s_, a_);                       \
     }
     LBK_GEDGE(7, 8, px + py, ux + uy)
     LBK_GEDGE(9, 10, px - py, ux - uy)

@@ -156,6 +156,85 @@ __device__ __forceinline__ df64 fmadd_sum(df64 a, df64 b, df64 c, df64 d)
     return r;
 }
 
+// Two floats in one 64-bit register (the first value in the low half) and
+// the paired FP32 instructions of sm_100 and later (add/sub/mul/fma
+// .rn.f32x2): one issue computes both halves, each rounded as its scalar
+// instruction would be.  Plain asm with outputs only, so the compiler may
+// merge or drop them like ordinary arithmetic.
+namespace px2 {
+
+__device__ __forceinline__ unsigned long long pack(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack(unsigned long long v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long add(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long sub(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long mul(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ void two_sum(unsigned long long a, unsigned long long b, unsigned long long &s,
+                                        unsigned long long &e)
+{
+    s = add(a, b);
+    const unsigned long long bb = sub(s, a);
+    e = add(sub(a, sub(s, bb)), sub(b, bb));
+}
+
+}  // namespace px2
+
+// The relaxation of an opposite pair, fp = c fp + (s + a) and
+// fm = c fm + (s - a), each fmadd_sum's float sequence, both values through
+// one pass of paired FP32 instructions (bitwise the two fmadd_sum results;
+// half the issue slots for this part of the collision).
+__device__ __forceinline__ void relax_pair(df64 c, df64 &fp, df64 &fm, df64 s, df64 a)
+{
+    using namespace px2;
+    const unsigned long long ch = pack(c.hi, c.hi), cl = pack(c.lo, c.lo);
+    const unsigned long long bh = pack(fp.hi, fm.hi), bl = pack(fp.lo, fm.lo);
+    const unsigned long long sh = pack(s.hi, s.hi), sl = pack(s.lo, s.lo);
+    const unsigned long long ah = pack(a.hi, -a.hi), al = pack(a.lo, -a.lo);
+    const unsigned long long p = mul(ch, bh);
+    float p0, p1;
+    unpack(p, p0, p1);
+    unsigned long long e = fma(ch, bh, pack(-p0, -p1));
+    e = fma(ch, bl, e);
+    e = fma(cl, bh, e);
+    unsigned long long s1, t1, sum, t2;
+    two_sum(sh, ah, s1, t1);
+    two_sum(p, s1, sum, t2);
+    const unsigned long long t = add(add(t1, t2), add(e, add(sl, al)));
+    // fast two-sum of (sum, t)
+    const unsigned long long rh = add(sum, t);
+    const unsigned long long rl = sub(t, sub(rh, sum));
+    unpack(rh, fp.hi, fm.hi);
+    unpack(rl, fp.lo, fm.lo);
+}
+
 __device__ __forceinline__ df64 &operator+=(df64 &a, df64 b) { return a = a + b; }
 __device__ __forceinline__ df64 &operator-=(df64 &a, df64 b) { return a = a - b; }
 __device__ __forceinline__ df64 &operator*=(df64 &a, df64 b) { return a = a * b; }
