@@ -80,6 +80,8 @@ def _peaks():
 
 
 # sources the default timestep's kernels are compiled from
+TIMING_NOTE = ("launch duration = the timed region's steps run back to back, CUDA events around them, "
+               "divided by their number; frac_single_launches: single steps each between two events")
 STEP_SOURCES = ("d3q19.cuh", "lb_site.cuh", "lb_coll.cuh", "lb_pdl.cuh", "lb_kernels.cu")
 
 
@@ -493,8 +495,11 @@ def run_ours(args):
             wall = max_over_ranks(start.elapsed_time(stop) / 1e3, ws)
             r = lat.reduce()
         t_launch = float(np.mean(per))
-        results[prec] = dict(cfg=cfg, wall=wall, t_launch=t_launch, clocks=clk.summary(),
-                             mass=float(r[0]))
+        # the roofline's launch duration: the timed region's steps back to
+        # back (CUDA events around them) over their number; t_launch, single
+        # steps each bracketed by events, is reported beside it
+        results[prec] = dict(cfg=cfg, wall=wall, t_step=wall / args.steps, t_launch=t_launch,
+                             clocks=clk.summary(), mass=float(r[0]))
 
     def timed(prec, kernel, npts, mrt=None):
         """Whole-run and per-step times of `kernel` (a name or a full launch
@@ -518,7 +523,7 @@ def run_ours(args):
                 barrier()
             wall = max_over_ranks(start.elapsed_time(stop) / 1e3, ws)
             per = _time_steps(lat, max(5, min(k, 20)), torch)
-        return dict(wall=wall, steps=k, t_launch=float(np.mean(per)), clocks=clk.summary())
+        return dict(wall=wall, steps=k, t_step=wall / k, t_launch=float(np.mean(per)), clocks=clk.summary())
 
     # the tau_g = 1 reduced form on the same workload (the workload has tau_g = 1)
     # (its phi pass's launch shape tuned here on first use)
@@ -633,32 +638,34 @@ def run_ours(args):
         # ncu summary of the kernel that ran (bulk: its own, with its sources listed)
         prof = f"step_bulk_{prec}_256cubed" if r["cfg"][0] == "bulk" else f"step_{prec}_256cubed"
         if prec == "fp32_shifted":
-            achieved = BYTES_PER_SITE[prec] * n / r["t_launch"] / 1e9
+            achieved = BYTES_PER_SITE[prec] * n / r["t_step"] / 1e9
             roof = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": _profile_value(prof, "dram_bytes_per_step"),
                     "peak_kind": f"{peak_kind} (copy bandwidth)",
-                    "algorithmic_bytes_per_launch": BYTES_PER_SITE[prec] * n}
+                    "algorithmic_bytes_per_launch": BYTES_PER_SITE[prec] * n,
+                    "launch_seconds": r["t_step"], "timing": TIMING_NOTE,
+                    "frac_single_launches": BYTES_PER_SITE[prec] * n / r["t_launch"] / 1e9 / peak}
         else:
             # FP64 is bound by the FP64 pipe: flops per site from ncu counters
             fl = _profile_value(prof, "fp64_flops_per_site")
             pk = fp64_peak["tflops"]
-            achieved = fl * n / r["t_launch"] / 1e12 if fl else None
+            achieved = fl * n / r["t_step"] / 1e12 if fl else None
             ins = _profile_value(prof, "fp64_instr_per_site")
             roof = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
                     "frac": (achieved / pk) if (achieved and pk) else None,
                     # FP64 adds and multiplies occupy the pipe like an FMA: the
                     # instruction rate against the FMA-instruction peak (peak / 2)
-                    "pipe_frac": (ins * n / r["t_launch"] / (pk * 1e12 / 2)) if (ins and pk) else None,
+                    "pipe_frac": (ins * n / r["t_step"] / (pk * 1e12 / 2)) if (ins and pk) else None,
                     "traffic": _profile_value(prof, "dram_bytes_per_step"),
                     "peak_kind": "measured in this run: FP64 FMA throughput of lb_probe_fp64_fma",
                     "peak_probe": fp64_peak,
-                    "hbm_frac": BYTES_PER_SITE[prec] * n / r["t_launch"] / 1e9 / peak}
+                    "hbm_frac": BYTES_PER_SITE[prec] * n / r["t_step"] / 1e9 / peak}
         return mlups, roof
 
     def reduced_for(prec):
         r = reduced[prec]
         bpl = BYTES_PER_SITE_TAUG1[prec] * n
-        achieved = bpl / r["t_launch"] / 1e9
+        achieved = bpl / r["t_step"] / 1e9
         return {"value": ws * n * r["steps"] / r["wall"] / 1e6, "unit": "MLUPS", "steps": r["steps"],
                 "ms_per_step": r["wall"] / r["steps"] * 1e3, "clocks": r["clocks"],
                 "roofline": {"bound": "hbm" if prec == "fp32_shifted" else "alu (FP64 pipe)",
@@ -666,14 +673,15 @@ def run_ours(args):
                              "unit": "GB/s", "frac": achieved / peak,
                              "traffic": _profile_value("step_taug1_256cubed", f"dram_bytes_per_step_{prec}"),
                              "peak_kind": f"{peak_kind} (copy bandwidth)",
-                             "algorithmic_bytes_per_launch": bpl},
+                             "algorithmic_bytes_per_launch": bpl, "launch_seconds": r["t_step"],
+                             "timing": TIMING_NOTE, "frac_single_launches": bpl / r["t_launch"] / 1e9 / peak},
                 "launch": tuned_t1[prec]["config"], "tuned_now": tuned_t1[prec]["tuned_now"],
                 "tuning_seconds": tuned_t1[prec]["seconds"],
                 "tuning_table": tuned_t1[prec]["table"]}
 
     def stencil_for(npts, prec):
         r = stencils[(npts, prec)]
-        achieved = BYTES_PER_SITE[prec] * n / r["t_launch"] / 1e9
+        achieved = BYTES_PER_SITE[prec] * n / r["t_step"] / 1e9
         out = {"value": ws * n * r["steps"] / r["wall"] / 1e6, "unit": "MLUPS", "steps": r["steps"],
                "ms_per_step": r["wall"] / r["steps"] * 1e3, "clocks": r["clocks"],
                "hbm_frac": achieved / peak, "achieved_gbs": achieved}
@@ -681,13 +689,13 @@ def run_ours(args):
             fl = _profile_value("step_isotropic_stencils_256cubed", f"fp64_flops_per_site_{npts}")
             pk = fp64_peak["tflops"]
             if fl and pk:
-                out["alu"] = {"achieved_tflops": fl * n / r["t_launch"] / 1e12, "peak_tflops": pk,
-                              "frac": fl * n / r["t_launch"] / 1e12 / pk, "flops_per_site": fl}
+                out["alu"] = {"achieved_tflops": fl * n / r["t_step"] / 1e12, "peak_tflops": pk,
+                              "frac": fl * n / r["t_step"] / 1e12 / pk, "flops_per_site": fl}
         return out
 
     def mrt_for(prec):
         r = mrt[prec]
-        achieved = BYTES_PER_SITE[prec] * n / r["t_launch"] / 1e9
+        achieved = BYTES_PER_SITE[prec] * n / r["t_step"] / 1e9
         out = {"value": ws * n * r["steps"] / r["wall"] / 1e6, "unit": "MLUPS", "steps": r["steps"],
                "ms_per_step": r["wall"] / r["steps"] * 1e3, "clocks": r["clocks"],
                "hbm_frac": achieved / peak, "achieved_gbs": achieved}
@@ -695,13 +703,13 @@ def run_ours(args):
             fl = _profile_value("step_mrt_256cubed", "fp64_flops_per_site")
             pk = fp64_peak["tflops"]
             if fl and pk:
-                out["alu"] = {"achieved_tflops": fl * n / r["t_launch"] / 1e12, "peak_tflops": pk,
-                              "frac": fl * n / r["t_launch"] / 1e12 / pk, "flops_per_site": fl}
+                out["alu"] = {"achieved_tflops": fl * n / r["t_step"] / 1e12, "peak_tflops": pk,
+                              "frac": fl * n / r["t_step"] / 1e12 / pk, "flops_per_site": fl}
         return out
 
     def df_line():
         r = df
-        achieved = BYTES_PER_SITE["fp64"] * n / r["t_launch"] / 1e9
+        achieved = BYTES_PER_SITE["fp64"] * n / r["t_step"] / 1e9
         return {"value": ws * n * r["steps"] / r["wall"] / 1e6, "unit": "MLUPS", "steps": r["steps"],
                 "ms_per_step": r["wall"] / r["steps"] * 1e3, "clocks": r["clocks"],
                 "speedup_vs_fp64": (r["steps"] / r["wall"]) / (args.steps / results["fp64"]["wall"]),
