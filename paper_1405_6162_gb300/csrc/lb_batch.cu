@@ -72,7 +72,10 @@ struct LatDesc {
     Coll<T> p;
 };
 
-constexpr int kBatchT1Kzc = 8;   // z run of a reduced-form phi tile in the ensemble
+#ifndef LBK_BATCH_T1_KZC
+#define LBK_BATCH_T1_KZC 8
+#endif
+constexpr int kBatchT1Kzc = LBK_BATCH_T1_KZC;   // z run of a reduced-form phi tile in the ensemble
 constexpr int kBatchPhiV = LBK_BATCH_PHI_V;   // phi-pass work items per trip (general form)
 
 struct GridBarrier {
