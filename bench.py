@@ -380,6 +380,39 @@ def _ensemble(torch, with_oracle=True):
         return out
 
 
+def _reverse_steps(torch, dims, nsteps, warmup=3):
+    """Seconds per reverse step (lb_adjoint_step through the C ABI, CUDA
+    events around nsteps calls after warmup ones) on the FP64 lattice dims
+    advanced 3 steps from a spinodal start, with seeded adjoint inputs."""
+    from paper_1405_6162_gb300 import Lattice, _lib as LL
+    params = dict(LI.DEFAULT_PARAMS)
+    n = int(np.prod(dims))
+    lib = LL.lib()
+    with Lattice.from_params(dims, params, precision="fp64") as lat:
+        lat.init(LI.spinodal_phi0(*dims, seed=6))
+        lat.step(3)
+        f, g = lat.get_state(device=True)
+        cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        a_in = [cu(LI.uniform(7 + k, 19 * n, -1.0, 1.0)) for k in range(2)]
+        a_out = [torch.empty(19 * n, dtype=torch.float64, device="cuda") for _ in range(2)]
+        dk = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+        def call():
+            rc = lib.lb_adjoint_step(lat.handle, f.data_ptr(), g.data_ptr(), a_in[0].data_ptr(), a_in[1].data_ptr(),
+                                     a_out[0].data_ptr(), a_out[1].data_ptr(), dk.data_ptr())
+            assert rc == 0, rc
+        for _ in range(warmup):
+            call()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(nsteps):
+            call()
+        e.record()
+        e.synchronize()
+        return s.elapsed_time(e) / 1e3 / nsteps
+
+
 def _adjoint(torch):
     """Gradient of sum (phi_T - phi_target)^2 wrt phi0 and kappa, 64^3,
     T = 200, FP64, sqrt(T) checkpoints; forward-only time for reference."""
@@ -435,7 +468,22 @@ def _adjoint(torch):
     fd = [central(h) for h in (2e-5, 1e-5)]
     fd_rich = (4 * fd[1] - fd[0]) / 3
     g = kap.grad.item()
+    # the reverse step against the FP64 pipe: flops per site from ncu counters
+    # (profiles/adjoint_reverse_step_64cubed.md), time of 50 steps here
+    t_rev = _reverse_steps(torch, dims, 50)
+    fl = _profile_value("adjoint_reverse_step_64cubed", "fp64_flops_per_site", True)
+    ins = _profile_value("adjoint_reverse_step_64cubed", "fp64_instr_per_site", True)
+    pk = _fp64_peak(torch)["tflops"]
+    n = int(np.prod(dims))
+    rev = {"seconds_per_step": t_rev,
+           "roofline": {"bound": "alu (FP64 pipe)", "kernels": "k_phi_local + k_adj_collide + k_adj_stencil + k_adj_kappa",
+                        "achieved": fl * n / t_rev / 1e12 if fl else None, "peak": pk, "unit": "TFLOP/s",
+                        "frac": fl * n / t_rev / 1e12 / pk if (fl and pk) else None, "flops_per_site": fl,
+                        "pipe_frac": ins * n / t_rev / (pk * 1e12 / 2) if (ins and pk) else None,
+                        "peak_kind": "measured in this run: FP64 FMA throughput of lb_probe_fp64_fma",
+                        "note": "64^3 FP64 state (80 MB) is L2-resident; the bound is the FP64 pipe"}}
     return {"lattice": list(dims), "steps": T, "precision": "fp64", "checkpoints": "every 14 steps (~sqrt T)",
+            "reverse_step": rev,
             "forward_s": t_fwd, "forward_backward_s": t_all, "ratio": t_all / t_fwd,
             "forward_backward_every_state_kept_s": t_store,
             "recompute_overhead": (t_all - t_store) / t_store,
@@ -824,6 +872,17 @@ def run_ensemble_only(args):
         print(json.dumps({"only": "ensemble", "lattices": len(specs), "sites": b.sites, "steps": args.steps}))
 
 
+def run_adjoint_only(args):
+    """``--steps`` reverse steps (lb_adjoint_step) of the --lattice FP64
+    lattice after 3 warm-up calls (a profiling case)."""
+    import torch
+    import paper_1405_6162_gb300 as lbpkg
+    lbpkg.build()
+    dims = tuple(args.lattice) * 3 if len(args.lattice) == 1 else tuple(args.lattice)
+    t = _reverse_steps(torch, dims, args.steps)
+    print(json.dumps({"only": "adjoint", "lattice": list(dims), "steps": args.steps, "seconds_per_step": t}))
+
+
 def run_fp64_peak_only(args):
     """The FP64 FMA-throughput probe alone (the FP64 roofline's peak)."""
     import torch
@@ -873,9 +932,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--only", choices=["step", "ensemble", "fp64-peak"], default=None,
+    ap.add_argument("--only", choices=["step", "ensemble", "fp64-peak", "adjoint"], default=None,
                     help="run only timesteps of one lattice, or of the 64-lattice ensemble in both forms "
-                         "(profiling cases), or the FP64 FMA-throughput probe")
+                         "(profiling cases), the FP64 FMA-throughput probe, or reverse steps of the adjoint")
     ap.add_argument("--lattice", type=int, nargs="+", default=[128],
                     help="edge of the --only lattice, or its three extents")
     ap.add_argument("--precision", choices=["fp32_shifted", "fp64", "fp64_df"], default="fp32_shifted")
@@ -893,6 +952,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.only == "ensemble":
         return run_ensemble_only(args)
+    if args.only == "adjoint":
+        return run_adjoint_only(args)
     if args.only == "fp64-peak":
         return run_fp64_peak_only(args)
     if args.only == "step":

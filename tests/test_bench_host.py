@@ -59,5 +59,6 @@ def test_committed_step_summaries_are_current():
                       ("step_fp64_df_256cubed", "dram_bytes_per_step"),
                       ("step_taug1_256cubed", "dram_bytes_per_step_fp32_shifted"),
                       ("step_mrt_256cubed", "fp64_flops_per_site"),
-                      ("step_isotropic_stencils_256cubed", "fp64_flops_per_site_27")):
+                      ("step_isotropic_stencils_256cubed", "fp64_flops_per_site_27"),
+                      ("adjoint_reverse_step_64cubed", "fp64_flops_per_site")):
         assert bench._profile_value(name, key) is not None, (name, key)
