@@ -413,6 +413,22 @@ def _reverse_steps(torch, dims, nsteps, warmup=3):
         return s.elapsed_time(e) / 1e3 / nsteps
 
 
+def _reduce_seconds(torch, lat, reps=10, warmup=3):
+    """Median seconds of one lb_reduce call on ``lat`` (CUDA events around
+    each call; a call is the per-block kernel, the final kernel, the 40-byte
+    read-back and the return to the host)."""
+    out = []
+    for k in range(warmup + reps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        lat.reduce()
+        e.record()
+        e.synchronize()
+        if k >= warmup:
+            out.append(s.elapsed_time(e) / 1e3)
+    return float(np.median(out))
+
+
 def _adjoint(torch):
     """Gradient of sum (phi_T - phi_target)^2 wrt phi0 and kappa, 64^3,
     T = 200, FP64, sqrt(T) checkpoints; forward-only time for reference."""
@@ -542,12 +558,13 @@ def run_ours(args):
                 per = _time_steps(lat, max(20, min(args.steps, 40)), torch)
             wall = max_over_ranks(start.elapsed_time(stop) / 1e3, ws)
             r = lat.reduce()
+            t_reduce = _reduce_seconds(torch, lat)
         t_launch = float(np.mean(per))
         # the roofline's launch duration: the timed region's steps back to
         # back (CUDA events around them) over their number; t_launch, single
         # steps each bracketed by events, is reported beside it
         results[prec] = dict(cfg=cfg, wall=wall, t_step=wall / args.steps, t_launch=t_launch,
-                             clocks=clk.summary(), mass=float(r[0]))
+                             clocks=clk.summary(), mass=float(r[0]), t_reduce=t_reduce)
 
     def timed(prec, kernel, npts, mrt=None):
         """Whole-run and per-step times of `kernel` (a name or a full launch
@@ -755,6 +772,27 @@ def run_ours(args):
                               "frac": fl * n / r["t_step"] / 1e12 / pk, "flops_per_site": fl}
         return out
 
+    def reduce_for(prec):
+        # lb_reduce is bound by the FP64 pipe: FP64 additions per site from
+        # ncu counters against the measured FP64 FMA-instruction rate (the
+        # probe's TFLOP/s over 2); the HBM fraction of its 38 stored words
+        # a site is given beside it
+        t = results[prec]["t_reduce"]
+        adds = _profile_value("reduce_128cubed", f"fp64_adds_per_site_{prec}")
+        pk = fp64_peak["tflops"]
+        gbs = 38 * (4 if prec == "fp32_shifted" else 8) * n / t / 1e9
+        ach = adds * n / t / 1e12 if adds else None
+        tr = _profile_value("reduce_128cubed", f"dram_bytes_per_site_{prec}")
+        return {"ms_per_call": t * 1e3, "sites_per_s": n / t,
+                "roofline": {"bound": "alu (FP64 pipe)", "kernel": "k_reduce_partial", "achieved": ach,
+                             "peak": pk / 2 if pk else None, "unit": "T FP64 instructions/s",
+                             "frac": ach / (pk / 2) if (ach and pk) else None, "fp64_adds_per_site": adds,
+                             "peak_kind": "measured in this run: FMA instructions/s of lb_probe_fp64_fma",
+                             "achieved_gbs": gbs, "hbm_frac": gbs / peak,
+                             "traffic": tr * n if tr else None,
+                             "timing": "median of 10 calls, CUDA events around each (both kernels, the "
+                                       "40-byte read-back and the return)"}}
+
     def df_line():
         r = df
         achieved = BYTES_PER_SITE["fp64"] * n / r["t_step"] / 1e9
@@ -799,6 +837,9 @@ def run_ours(args):
         "mrt": {"what": f"multiple-relaxation-time collision of f (lb_set_collision), tau = 1, "
                         f"tau_bulk = {MRT_RATES[0]}, tau_ghost = {MRT_RATES[1]}, on the default two-pass step",
                 "fp32_shifted": mrt_for("fp32_shifted"), "fp64": mrt_for("fp64")},
+        "reductions": {"what": "lb_reduce: FP64 totals of rho, rho u and phi over the 256^3 lattice of each "
+                               "precision after the timed steps",
+                       "fp32_shifted": reduce_for("fp32_shifted"), "fp64": reduce_for("fp64")},
         "masked_moments": {"what": "lb_moments_masked (stream compaction: count, scan, gather) of a seeded "
                                    "random site mask on the 256^3 FP32 lattice, device outputs, one call "
                                    "includes the read-back of the count",
@@ -883,6 +924,23 @@ def run_adjoint_only(args):
     print(json.dumps({"only": "adjoint", "lattice": list(dims), "steps": args.steps, "seconds_per_step": t}))
 
 
+def run_reduce_only(args):
+    """``--steps`` lb_reduce calls on the --lattice lattice of --precision
+    after a spinodal start and --warmup timesteps (a profiling case)."""
+    import torch
+    import paper_1405_6162_gb300 as lbpkg
+    from paper_1405_6162_gb300 import Lattice
+    lbpkg.build()
+    dims = tuple(args.lattice) * 3 if len(args.lattice) == 1 else tuple(args.lattice)
+    with Lattice.from_params(dims, dict(LI.DEFAULT_PARAMS), precision=args.precision) as lat:
+        lat.init(LI.spinodal_phi0(*dims, seed=1))
+        lat.step(args.warmup)
+        t = _reduce_seconds(torch, lat, reps=args.steps)
+        tot = lat.reduce()
+    print(json.dumps({"only": "reduce", "lattice": list(dims), "precision": args.precision, "calls": args.steps,
+                      "seconds_per_call": t, "totals": [float(x) for x in tot]}))
+
+
 def run_fp64_peak_only(args):
     """The FP64 FMA-throughput probe alone (the FP64 roofline's peak)."""
     import torch
@@ -932,9 +990,10 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--only", choices=["step", "ensemble", "fp64-peak", "adjoint"], default=None,
+    ap.add_argument("--only", choices=["step", "ensemble", "fp64-peak", "adjoint", "reduce"], default=None,
                     help="run only timesteps of one lattice, or of the 64-lattice ensemble in both forms "
-                         "(profiling cases), the FP64 FMA-throughput probe, or reverse steps of the adjoint")
+                         "(profiling cases), the FP64 FMA-throughput probe, reverse steps of the adjoint, "
+                         "or lattice totals (lb_reduce) of one lattice")
     ap.add_argument("--lattice", type=int, nargs="+", default=[128],
                     help="edge of the --only lattice, or its three extents")
     ap.add_argument("--precision", choices=["fp32_shifted", "fp64", "fp64_df"], default="fp32_shifted")
@@ -956,6 +1015,8 @@ def main():
         return run_adjoint_only(args)
     if args.only == "fp64-peak":
         return run_fp64_peak_only(args)
+    if args.only == "reduce":
+        return run_reduce_only(args)
     if args.only == "step":
         run_step_only(args)
     elif args.impl == "reference":

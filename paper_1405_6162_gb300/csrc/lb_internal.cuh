@@ -98,7 +98,7 @@ inline Mrt<T> make_mrt(const lb_ctx *c)
 
 constexpr int kLagBlock = 256;       // sites per block of the lagged kernel
 constexpr long long kLagSlack = 128;  // extra lag (blocks) beyond the stencil reach
-constexpr int kReduceBlocks = 608;   // 4 x 152 SMs; fixed so sums are reproducible
+constexpr int kReduceBlocks = 304;   // 2 x 152 SMs, one wave; fixed so sums are reproducible
 constexpr int kReduceThreads = 256;
 
 // ensemble membership (lb_api.cu): the member shares the batch's error flag

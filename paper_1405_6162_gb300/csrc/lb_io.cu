@@ -151,29 +151,59 @@ __device__ __forceinline__ void block_sum(double (&acc)[K], double *out)
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kReduceThreads) k_reduce_partial(const T *__restrict__ fa,
-                                                                   const T *__restrict__ ga,
-                                                                   long long N, long long S, int g_rows,
-                                                                   double *__restrict__ partial)
+// A stored value widened to FP64 exactly.  float: from the IEEE 754
+// binary32 and binary64 layouts -- sign and fraction kept (the fraction
+// moved up 29 bits), the exponent rebiased by 1023 - 127 = 896; a subnormal
+// is first scaled by 2^64 (exact in FP32, and normal) and rebiased by 64
+// less; zero keeps its sign, infinity stays infinite and NaN becomes a quiet
+// NaN.  Integer and FP32 operations only: on GB300 the conversion
+// instruction runs on the FP64 pipe (about 2 lanes a clock per SM), where it
+// would double this kernel's FP64 work.
+__device__ __forceinline__ double widen(float x)
 {
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const unsigned u = __float_as_uint(x), a = u & 0x7fffffffu;
+    const bool sub = a < 0x00800000u;   // zero or subnormal
+    const unsigned v = sub ? (__float_as_uint(x * 0x1p64f) & 0x7fffffffu) : a;
+    unsigned hi = (v >> 3) + (sub ? 0x34000000u : 0x38000000u);
+    hi = v ? hi : 0u;
+    if (a >= 0x7f800000u) hi = (a >> 3) | 0x7ff00000u | (a > 0x7f800000u ? 0x00080000u : 0u);
+    return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)(v << 29));
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+// hi + lo of a double-float is exact in FP64 (|lo| <= ulp(hi) / 2)
+__device__ __forceinline__ double widen(df64 x) { return widen(x.hi) + widen(x.lo); }
+
+// Per-block partial totals.  A thread sums each of the 19 f rows over its
+// sites in FP64 (sum_x A_i(x)), and the g rows (G rows: 19, or 1 in the
+// tau_g = 1 reduced form, whose row 0 holds phi) into four FP64 partial
+// sums, as only their total, sum phi, is wanted; R and j = sum_i c_i F_i are
+// formed from the 19 row totals once per thread.  That is 38 FP64 additions
+// a site (plus one per float of a double-float) against the 68 that forming
+// every site's moments takes.  The order of every addition is fixed by the
+// launch shape, so the totals are bitwise reproducible.
+template <typename T, int G_ROWS>
+__global__ void __launch_bounds__(kReduceThreads, 2) k_reduce_partial(const T *__restrict__ fa,
+                                                                      const T *__restrict__ ga, long long N,
+                                                                      long long S, double *__restrict__ partial)
+{
+    double F[Q], G[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < Q; i++) F[i] = 0.0;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < N;
          s += (long long)gridDim.x * blockDim.x) {
-        double f[Q], g[Q];
+        T f[Q], g[G_ROWS];
 #pragma unroll
-        for (int i = 0; i < Q; i++) {
-            f[i] = double(fa[(size_t)i * S + s]);
-            g[i] = i < g_rows ? double(ga[(size_t)i * S + s]) : 0.0;   // reduced form: phi in row 0
-        }
-        double R, jx, jy, jz;
-        density_moments(f, R, jx, jy, jz);
-        acc[0] += R;
-        acc[1] += jx;
-        acc[2] += jy;
-        acc[3] += jz;
-        acc[4] += sum19(g);
+        for (int i = 0; i < Q; i++) f[i] = fa[(size_t)i * S + s];
+#pragma unroll
+        for (int i = 0; i < G_ROWS; i++) g[i] = ga[(size_t)i * S + s];
+#pragma unroll
+        for (int i = 0; i < Q; i++) F[i] += widen(f[i]);
+#pragma unroll
+        for (int i = 0; i < G_ROWS; i++) G[i & 3] += widen(g[i]);
     }
+    double acc[5];
+    density_moments(F, acc[0], acc[1], acc[2], acc[3]);
+    acc[4] = (G[0] + G[1]) + (G[2] + G[3]);
     block_sum<5>(acc, partial + 5 * blockIdx.x);
 }
 
@@ -296,8 +326,11 @@ int launch_reduce(lb_ctx *c, double *dev_out5)
     const double off = c->p.precision == LB_FP32_SHIFTED ? double(c->N) * c->p.rho0 : 0.0;
     int rc = by_precision(c, [&](auto P) {
         using T = typename decltype(P)::T;
-        k_reduce_partial<T><<<kReduceBlocks, kReduceThreads, 0, c->stream>>>(
-            (const T *)c->buf.f[cur], (const T *)c->buf.g[cur], c->N, c->S, c->reduced ? 1 : Q, c->partial);
+        const T *fa = (const T *)c->buf.f[cur], *ga = (const T *)c->buf.g[cur];
+        if (c->reduced)
+            k_reduce_partial<T, 1><<<kReduceBlocks, kReduceThreads, 0, c->stream>>>(fa, ga, c->N, c->S, c->partial);
+        else
+            k_reduce_partial<T, Q><<<kReduceBlocks, kReduceThreads, 0, c->stream>>>(fa, ga, c->N, c->S, c->partial);
         return check_launch();
     });
     if (rc) return rc;

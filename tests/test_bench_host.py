@@ -60,5 +60,7 @@ def test_committed_step_summaries_are_current():
                       ("step_taug1_256cubed", "dram_bytes_per_step_fp32_shifted"),
                       ("step_mrt_256cubed", "fp64_flops_per_site"),
                       ("step_isotropic_stencils_256cubed", "fp64_flops_per_site_27"),
-                      ("adjoint_reverse_step_64cubed", "fp64_flops_per_site")):
+                      ("adjoint_reverse_step_64cubed", "fp64_flops_per_site"),
+                      ("reduce_128cubed", "fp64_adds_per_site_fp32_shifted"),
+                      ("reduce_128cubed", "dram_bytes_per_site_fp64")):
         assert bench._profile_value(name, key) is not None, (name, key)

@@ -189,19 +189,53 @@ def test_reductions_match_oracle_and_conserve():
     assert np.abs(r1[1:] - r0[1:]).max() <= 1e-13 * r0[0]
 
 
-def test_nonfinite_state_is_reported():
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+def test_nonfinite_state_is_reported(bad):
     from paper_1405_6162_gb300 import LBError
     from paper_1405_6162_gb300 import _lib as LL
     dims = (8, 8, 8)
     f0, g0 = nonequilibrium_state(dims, P0, seed=70)
-    f0[3, 100] = np.nan
-    for precision in ("fp64", "fp32_shifted"):
+    f0[3, 100] = bad
+    for precision in ("fp64", "fp32_shifted", "fp64_df"):
         with gpu_lattice(dims, P0, precision) as lat:
             lat.set_state(to_abi(f0), to_abi(g0))
             with pytest.raises(LBError) as ei:
                 lat.reduce()
             assert ei.value.code == LL.LB_ERR_NONFINITE
             lat.step(1)       # the context stays usable after the report
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_shifted", "fp64_df"])
+def test_reduce_exact_totals(precision):
+    """A state on which every sum of stored values is exact in FP64, so the
+    totals are fixed to the bit whatever the order of the additions: f =
+    w_i rho0 + d with rho0 = 36/64 (w_i rho0 exact in binary) and d integer
+    multiples of 2^-24, a seventh of them zero (stored as +0 in the shifted
+    form); g integer multiples of 2^-140 (subnormal floats), a fifth of them
+    -0.  The widening of each stored float to FP64 must be exact for every
+    such class of value."""
+    import math
+    from paper_1405_6162_gb300 import VELOCITIES
+    dims = (20, 12, 10)            # 2400 sites: a ragged last block of 256
+    n = int(np.prod(dims))
+    rho0 = 36.0 / 64.0
+    p = dict(P0, rho0=rho0)
+    c = np.asarray(VELOCITIES, dtype=float)
+    w = np.where((c ** 2).sum(1) == 0, 1 / 3, np.where((c ** 2).sum(1) == 1, 1 / 18, 1 / 36))
+    rng = np.random.default_rng(80)
+    d = rng.integers(-2 ** 16, 2 ** 16, size=(19, n)) * 2.0 ** -24
+    d[:, ::7] = 0.0
+    f = w[:, None] * rho0 + d
+    g = rng.integers(-2 ** 10, 2 ** 10, size=(19, n)) * 2.0 ** -140
+    g[:, ::5] = -0.0
+    assert np.array_equal(f - w[:, None] * rho0, d)          # the shift is exact
+    fi = [math.fsum(f[i]) for i in range(19)]
+    want = np.array([math.fsum(fi)] + [math.fsum(c[i, a] * fi[i] for i in range(19)) for a in range(3)]
+                    + [math.fsum(g.ravel())])
+    with gpu_lattice(dims, p, precision) as lat:
+        lat.set_state(f, g)
+        got = lat.reduce()
+    assert np.array_equal(got, want), (got, want)
 
 
 # ------------------------------------------------------------------ FP32 shifted
