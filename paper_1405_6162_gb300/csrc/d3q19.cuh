@@ -76,11 +76,16 @@ __host__ __device__ constexpr double weight(int i) {
 // the step evaluates f* = (1 - omega) f + omega feq with one multiply-add
 // per direction (likewise g with omega_g); they are computed in double on
 // the host and rounded once.
+// x / 2 (exact in binary floating point)
+__device__ __forceinline__ float half(float x) { return 0.5f * x; }
+__device__ __forceinline__ double half(double x) { return 0.5 * x; }
+
 template <typename T>
 struct Coll {
     T omega, omega_g;      // 1/tau, 1/tau_g
     T rho0;                // shift of the FP32 form
     T gamma, A, B, kappa;
+    T hA, qB;              // A/2, 3B/4 (the bulk pressure's coefficients)
     T cf, f0, f1, f2, f1h, f2h, f1t, f2t;   // 1-omega; omega*w_k; omega*w_k*9/2; omega*w_k*3
     T cg, g0, g1, g2, g1h, g2h, g1t, g2t;   // the same with omega_g
 };
@@ -183,7 +188,6 @@ __device__ __forceinline__ void collide_f(const Coll<T>& p, T (&f)[Q], T phi, T 
 {
     T R, jx, jy, jz;
     density_moments(f, R, jx, jy, jz);
-    const T third = T(1.0 / 3.0), h = T(4.5);
     const T rho = SH ? p.rho0 + R : R;
     const T rinv = T(1) / rho;
     ux = jx * rinv;
@@ -191,8 +195,7 @@ __device__ __forceinline__ void collide_f(const Coll<T>& p, T (&f)[Q], T phi, T 
     uz = jz * rinv;
     const T phi2 = phi * phi;
     mu = phi * (p.A + p.B * phi2) - p.kappa * lap;
-    const T pb = phi2 * (T(0.5) * p.A + T(0.75) * p.B * phi2)
-               - p.kappa * (phi * lap + T(0.5) * (dx * dx + dy * dy + dz * dz));
+    const T pb = phi2 * (p.hA + p.qB * phi2) - p.kappa * (phi * lap + half(dx * dx + dy * dy + dz * dz));
     // S = P + rho u u
     const T Sxx = pb + p.kappa * dx * dx + jx * ux;
     const T Syy = pb + p.kappa * dy * dy + jy * uy;
@@ -200,11 +203,11 @@ __device__ __forceinline__ void collide_f(const Coll<T>& p, T (&f)[Q], T phi, T 
     const T Sxy = p.kappa * dx * dy + jx * uy;
     const T Sxz = p.kappa * dx * dz + jx * uz;
     const T Syz = p.kappa * dy * dz + jy * uz;
-    const T t3 = (Sxx + Syy + Szz) * third;
 
-    // ---- f: omega feq_i = omega w_i (R - 9/2 t3) + 9/2 omega w_i c_i c_i : S + 3 omega w_i c_i . j
+    // ---- f: omega feq_i = omega w_i (R - 9/2 t3) + 9/2 omega w_i c_i c_i : S + 3 omega w_i c_i . j,
+    // t3 = tr S / 3, so 9/2 t3 = 3/2 tr S (3/2 exact in binary)
     const T cf = p.cf;
-    const T b = R - h * t3;
+    const T b = R - T(1.5) * (Sxx + Syy + Szz);
     f[0] = fmadd(cf, f[0], p.f0 * b);
     const T B1 = p.f1 * b, B2 = p.f2 * b;
 #define LBK_FACE(IP, IM, SAA, JA)                                  \
@@ -240,9 +243,8 @@ __device__ __forceinline__ void collide_g(const Coll<T>& p, T (&g)[Q], T phi, T 
     // ---- g: omega_g geq_i = omega_g w_i [phi + 3 phi c.u + 9/2 (phi (c.u)^2 - phi u^2/3 + (Gamma mu - phi/3)(c^2 - 1))]
     const T cg = p.cg;
     const T px = phi * ux, py = phi * uy, pz = phi * uz;
-    const T pu2 = (px * ux + py * uy + pz * uz) * third;
     const T gm = p.gamma * mu - phi * third;
-    const T bg = phi - h * pu2;
+    const T bg = phi - T(1.5) * (px * ux + py * uy + pz * uz);   // phi - 9/2 phi u^2 / 3
     g[0] = fmadd(cg, g[0], p.g0 * (bg - h * gm));
     const T G1 = p.g1 * bg, G2 = p.g2 * (bg + h * gm);
 #define LBK_GFACE(IP, IM, PA, UA)                                   \

@@ -65,97 +65,6 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &
 
 }  // namespace dfops
 
-#ifndef LBK_DF64_ACCURATE_ADD
-#define LBK_DF64_ACCURATE_ADD 0
-#endif
-
-__device__ __forceinline__ df64 operator+(df64 a, df64 b)
-{
-#if LBK_DF64_ACCURATE_ADD
-    // both component pairs summed exactly: error ~2^-48 of the result
-    float s1, s2, t1, t2;
-    dfops::two_sum(a.hi, b.hi, s1, s2);
-    dfops::two_sum(a.lo, b.lo, t1, t2);
-    s2 = __fadd_rn(s2, t1);
-    dfops::fast_two_sum(s1, s2, s1, s2);
-    s2 = __fadd_rn(s2, t2);
-    df64 r;
-    dfops::fast_two_sum(s1, s2, r.hi, r.lo);
-    return r;
-#else
-    // the high parts summed exactly, the low parts added to the error: error
-    // ~2^-48 of the larger operand (the absolute accuracy double arithmetic
-    // gives a sum of such operands)
-    float s, e;
-    dfops::two_sum(a.hi, b.hi, s, e);
-    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-    df64 r;
-    dfops::fast_two_sum(s, e, r.hi, r.lo);
-    return r;
-#endif
-}
-
-__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
-__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
-
-__device__ __forceinline__ df64 operator*(df64 a, df64 b)
-{
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-    df64 r;
-    dfops::fast_two_sum(p, e, r.hi, r.lo);
-    return r;
-}
-
-// a / b: a float quotient refined twice by the residual a - q b
-__device__ __forceinline__ df64 operator/(df64 a, df64 b)
-{
-    const float q1 = __fdiv_rn(a.hi, b.hi);
-    const df64 r1 = a - b * df64(q1, 0.0f);
-    const float q2 = __fdiv_rn(r1.hi, b.hi);
-    const df64 r2 = r1 - b * df64(q2, 0.0f);
-    const float q3 = __fdiv_rn(r2.hi, b.hi);
-    float s, e;
-    dfops::fast_two_sum(q1, q2, s, e);
-    return df64(s, e) + df64(q3, 0.0f);
-}
-
-// a * b + c with the product's error terms folded into the addition
-__device__ __forceinline__ df64 fmadd(df64 a, df64 b, df64 c)
-{
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-    float s, t;
-    dfops::two_sum(p, c.hi, s, t);
-    t = __fadd_rn(t, __fadd_rn(e, c.lo));
-    df64 r;
-    dfops::fast_two_sum(s, t, r.hi, r.lo);
-    return r;
-}
-
-// a * b + (c + d) renormalised once: the product's error terms, the two
-// exact sums' errors (c.hi + d.hi, then the product) and the low parts are
-// added to one error term (23 float operations instead of the 26 of
-// fmadd(a, b, c + d), the same ~2^-48 bound relative to the largest term)
-__device__ __forceinline__ df64 fmadd_sum(df64 a, df64 b, df64 c, df64 d)
-{
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-    float s1, t1, s, t2;
-    dfops::two_sum(c.hi, d.hi, s1, t1);
-    dfops::two_sum(p, s1, s, t2);
-    const float t = __fadd_rn(__fadd_rn(t1, t2), __fadd_rn(e, __fadd_rn(c.lo, d.lo)));
-    df64 r;
-    dfops::fast_two_sum(s, t, r.hi, r.lo);
-    return r;
-}
-
 // Two floats in one 64-bit register (the first value in the low half) and
 // the paired FP32 instructions of sm_100 and later (add/sub/mul/fma
 // .rn.f32x2): one issue computes both halves, each rounded as its scalar
@@ -206,6 +115,123 @@ __device__ __forceinline__ void two_sum(unsigned long long a, unsigned long long
 }
 
 }  // namespace px2
+
+#ifndef LBK_DF64_ACCURATE_ADD
+#define LBK_DF64_ACCURATE_ADD 0
+#endif
+
+__device__ __forceinline__ df64 operator+(df64 a, df64 b)
+{
+#if LBK_DF64_ACCURATE_ADD
+    // both component pairs summed exactly: error ~2^-48 of the result
+    float s1, s2, t1, t2;
+    dfops::two_sum(a.hi, b.hi, s1, s2);
+    dfops::two_sum(a.lo, b.lo, t1, t2);
+    s2 = __fadd_rn(s2, t1);
+    dfops::fast_two_sum(s1, s2, s1, s2);
+    s2 = __fadd_rn(s2, t2);
+    df64 r;
+    dfops::fast_two_sum(s1, s2, r.hi, r.lo);
+    return r;
+#else
+    // the high parts summed exactly, the low parts added to the error: error
+    // ~2^-48 of the larger operand (the absolute accuracy double arithmetic
+    // gives a sum of such operands)
+    float s, e;
+    dfops::two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    df64 r;
+    dfops::fast_two_sum(s, e, r.hi, r.lo);
+    return r;
+#endif
+}
+
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+
+// a + b bitwise as operator+ (the cheaper form), with the high parts' sum
+// and the low parts' sum issued as one paired instruction.  Whether that
+// pays depends on the kernel's register allocation (measured: the reduced
+// form's phi pass gains, the two-pass collision loses), so the kernels
+// choose it per call site.
+__device__ __forceinline__ df64 add_px(df64 a, df64 b)
+{
+    float s, l;
+    px2::unpack(px2::add(px2::pack(a.hi, a.lo), px2::pack(b.hi, b.lo)), s, l);
+    const float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    e = __fadd_rn(e, l);
+    df64 r;
+    dfops::fast_two_sum(s, e, r.hi, r.lo);
+    return r;
+}
+__device__ __forceinline__ df64 sub_px(df64 a, df64 b) { return add_px(a, -b); }
+__device__ __forceinline__ float add_px(float a, float b) { return a + b; }
+__device__ __forceinline__ float sub_px(float a, float b) { return a - b; }
+__device__ __forceinline__ double add_px(double a, double b) { return a + b; }
+__device__ __forceinline__ double sub_px(double a, double b) { return a - b; }
+
+__device__ __forceinline__ df64 operator*(df64 a, df64 b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    df64 r;
+    dfops::fast_two_sum(p, e, r.hi, r.lo);
+    return r;
+}
+
+// x / 2: both parts halved, exactly (barring underflow)
+__device__ __forceinline__ df64 half(df64 a) { return df64(0.5f * a.hi, 0.5f * a.lo); }
+
+// a / b: a float quotient refined twice by the residual a - q b
+__device__ __forceinline__ df64 operator/(df64 a, df64 b)
+{
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const df64 r1 = a - b * df64(q1, 0.0f);
+    const float q2 = __fdiv_rn(r1.hi, b.hi);
+    const df64 r2 = r1 - b * df64(q2, 0.0f);
+    const float q3 = __fdiv_rn(r2.hi, b.hi);
+    float s, e;
+    dfops::fast_two_sum(q1, q2, s, e);
+    return df64(s, e) + df64(q3, 0.0f);
+}
+
+// a * b + c with the product's error terms folded into the addition
+__device__ __forceinline__ df64 fmadd(df64 a, df64 b, df64 c)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    float s, t;
+    dfops::two_sum(p, c.hi, s, t);
+    t = __fadd_rn(t, __fadd_rn(e, c.lo));
+    df64 r;
+    dfops::fast_two_sum(s, t, r.hi, r.lo);
+    return r;
+}
+
+// a * b + (c + d) renormalised once: the product's error terms, the two
+// exact sums' errors (c.hi + d.hi, then the product) and the low parts are
+// added to one error term (23 float operations instead of the 26 of
+// fmadd(a, b, c + d), the same ~2^-48 bound relative to the largest term)
+__device__ __forceinline__ df64 fmadd_sum(df64 a, df64 b, df64 c, df64 d)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    float s1, t1, s, t2;
+    dfops::two_sum(c.hi, d.hi, s1, t1);
+    dfops::two_sum(p, s1, s, t2);
+    const float t = __fadd_rn(__fadd_rn(t1, t2), __fadd_rn(e, __fadd_rn(c.lo, d.lo)));
+    df64 r;
+    dfops::fast_two_sum(s, t, r.hi, r.lo);
+    return r;
+}
+
 
 // The relaxation of an opposite pair, fp = c fp + (s + a) and
 // fm = c fm + (s - a), each fmadd_sum's float sequence, both values through

@@ -21,6 +21,8 @@ inline Coll<T> make_coll(const lb_params &p)
     c.A = T(p.A);
     c.B = T(p.B);
     c.kappa = T(p.kappa);
+    c.hA = T(0.5 * p.A);
+    c.qB = T(0.75 * p.B);
     c.cf = T(1.0 - om);
     c.f0 = T(om / 3.0);  c.f1 = T(om / 18.0);  c.f2 = T(om / 36.0);
     c.f1h = T(om / 4.0); c.f2h = T(om / 8.0);

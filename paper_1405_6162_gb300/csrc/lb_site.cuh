@@ -45,9 +45,9 @@ __device__ __forceinline__ void stencil_np(const T *__restrict__ phi, const Nbr 
         const R xp = R(phi[n.at(1, 0, 0)]), xm = R(phi[n.at(-1, 0, 0)]);
         const R yp = R(phi[n.at(0, 1, 0)]), ym = R(phi[n.at(0, -1, 0)]);
         const R zp = R(phi[n.at(0, 0, 1)]), zm = R(phi[n.at(0, 0, -1)]);
-        dx = R(0.5) * (xp - xm);
-        dy = R(0.5) * (yp - ym);
-        dz = R(0.5) * (zp - zm);
+        dx = half(xp - xm);
+        dy = half(yp - ym);
+        dz = half(zp - zm);
         lap = ((xp + xm) + (yp + ym)) + (zp + zm) - R(6) * ph;
     } else {
         // per weight class k (1 faces, 2 edges, 3 corners): sum of phi and the

@@ -44,9 +44,9 @@ __device__ __forceinline__ T cdot(int i, T ux, T uy, T uz)
 {
     T r = cx(i) > 0 ? ux : -ux;
     if (cx(i) == 0) r = cy(i) > 0 ? uy : -uy;
-    else if (cy(i) != 0) r = cy(i) > 0 ? r + uy : r - uy;
+    else if (cy(i) != 0) r = cy(i) > 0 ? add_px(r, uy) : sub_px(r, uy);
     if (cx(i) == 0 && cy(i) == 0) r = cz(i) > 0 ? uz : -uz;
-    else if (cz(i) != 0) r = cz(i) > 0 ? r + uz : r - uz;
+    else if (cz(i) != 0) r = cz(i) > 0 ? add_px(r, uz) : sub_px(r, uz);
     return r;
 }
 
@@ -70,7 +70,42 @@ __device__ __forceinline__ T geq_eq(int i, const Eq<T> &e)
     }
     const T cu = cdot(i, e.ux, e.uy, e.uz);
     const T base = c2 == 1 ? e.b1 : e.b2;
-    return T(weight(i)) * (base + cu * (e.a3 + e.a45 * cu));
+    return T(weight(i)) * add_px(base, cu * add_px(e.a3, e.a45 * cu));
+}
+
+// The phi pass's form of the equilibria.  For an opposite pair (i, i + 1;
+// i odd, c_{i+1} = -c_i) with cu = c_i . u,
+//   geq_i = S + A,  geq_{i+1} = S - A,  S = w (b + 9/2 phi cu^2),  A = 3 w phi cu,
+// w and b those of the pair's weight class, so that a pair costs one S and
+// one A.  The class terms are formed once per source site.
+static_assert(cx(2) == -cx(1) && cy(4) == -cy(3) && cz(6) == -cz(5) && cx(8) == -cx(7) && cy(8) == -cy(7) &&
+                  cy(10) == -cy(9) && cz(12) == -cz(11) && cz(14) == -cz(13) && cy(16) == -cy(15) &&
+                  cz(16) == -cz(15) && cy(18) == -cy(17) && cz(18) == -cz(17),
+              "opposite directions are (i, i + 1), i odd");
+
+template <typename T>
+struct EqPair {
+    T r0;                       // geq_0
+    T wb[2], wq[2], wa[2];      // per class (faces, edges): w b, 9/2 w phi, 3 w phi
+    T ux, uy, uz;
+};
+
+template <typename T>
+__device__ __forceinline__ EqPair<T> pair_form(const Eq<T> &e)
+{
+    EqPair<T> p;
+    p.r0 = geq_eq(0, e);
+    const T w1 = T(weight(1)), w2 = T(weight(7));
+    p.wb[0] = w1 * e.b1;
+    p.wb[1] = w2 * e.b2;
+    p.wq[0] = w1 * e.a45;
+    p.wq[1] = w2 * e.a45;
+    p.wa[0] = w1 * e.a3;
+    p.wa[1] = w2 * e.a3;
+    p.ux = e.ux;
+    p.uy = e.uy;
+    p.uz = e.uz;
+    return p;
 }
 
 // the quad (gmh, u) of a site: one vector access
@@ -251,23 +286,53 @@ __device__ __forceinline__ void t1_phi_tile(const T *__restrict__ ga, T *__restr
             const int j = j0 + k;
             if (j >= nzc + 2) break;   // uniform over the warp
             const bool more = j + 1 < nzc + 2;   // uniform: plane j + 1 is part of the run
+            // the partial sum that direction i of source row ry feeds: output
+            // row ry + c_y, slot of output plane j - 1 + c_z, this column or
+            // (through the shuffles) column x + c_x
+            auto slot = [&](int i, int oy) -> T & {
+                const int q = (k + 2 + cz(i)) % 3;
+                return cx(i) == 0 ? acc[q][oy] : cx(i) > 0 ? acc_r[q][oy] : acc_l[q][oy];
+            };
 #pragma unroll
             for (int ry = -1; ry <= KY; ry++) {
                 T (&c5)[5] = raw[ry + 1];
                 const Eq<T> e = make_eq(c5[0], c5[1], c5[2], c5[3], c5[4]);
                 if (more) t1_load_site(ga, q0, zl + yoff[ry + 1], c5);
+                if constexpr (is_df64<T>::value) {
+                    // double-float: the pair form (measured: 7.59 against 6.21
+                    // GLUPS at 256^3; in float and double the compiler already
+                    // shares c.u between opposite directions, and the pair
+                    // form's longer-lived class terms cost occupancy there)
+                    const EqPair<T> ep = pair_form(e);
+                    if (ry >= 0 && ry < KY) {
+                        T &a = slot(0, ry);
+                        a = add_px(a, ep.r0);
+                    }
 #pragma unroll
-                for (int i = 0; i < Q; i++) {
-                    const int oy = ry + cy(i);
-                    if (oy < 0 || oy >= KY) continue;
-                    const int q = (k + 2 + cz(i)) % 3;   // slot of output plane j - 1 + c_z
-                    const T v = geq_eq(i, e);
-                    if (cx(i) == 0)
-                        acc[q][oy] += v;
-                    else if (cx(i) > 0)
-                        acc_r[q][oy] += v;   // to column x + 1
-                    else
-                        acc_l[q][oy] += v;   // to column x - 1
+                    for (int i = 1; i < Q; i += 2) {
+                        const int op = ry + cy(i), om = ry - cy(i);   // output rows of i and i + 1
+                        const bool hp = op >= 0 && op < KY, hm = om >= 0 && om < KY;
+                        if (!hp && !hm) continue;
+                        const int c = i <= 6 ? 0 : 1;
+                        const T cu = cdot(i, ep.ux, ep.uy, ep.uz);
+                        const T S = fmadd(ep.wq[c] * cu, cu, ep.wb[c]);
+                        if (hp) {
+                            T &a = slot(i, op);
+                            a = fmadd(ep.wa[c], cu, add_px(a, S));    // + S + A
+                        }
+                        if (hm) {
+                            T &a = slot(i + 1, om);
+                            a = fmadd(-ep.wa[c], cu, add_px(a, S));   // + S - A
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < Q; i++) {
+                        const int oy = ry + cy(i);
+                        if (oy < 0 || oy >= KY) continue;
+                        T &a = slot(i, oy);
+                        a += geq_eq(i, e);
+                    }
                 }
             }
             if (more) {
@@ -282,7 +347,7 @@ __device__ __forceinline__ void t1_phi_tile(const T *__restrict__ ga, T *__restr
                 const T from_left = shfl_up1(acc_r[qd][a]);
                 const T from_right = shfl_down1(acc_l[qd][a]);
                 if (out_x && oz >= 0 && y0 + a < ny)
-                    gb[yoff[a + 1] + (z0 + oz) * plane] = acc[qd][a] + (from_left + from_right);
+                    gb[yoff[a + 1] + (z0 + oz) * plane] = add_px(acc[qd][a], add_px(from_left, from_right));
                 acc[qd][a] = acc_r[qd][a] = acc_l[qd][a] = T(0);
             }
         }
