@@ -29,21 +29,24 @@ def _setup():
 
 
 # the two-pass step, the bulk-copy single pass (the kernels the benchmark's
-# autotuner chooses between at 256^3, in their default shapes), the library
-# default (the bulk kernel in FP32, the two-pass step in FP64) and the
-# tau_g = 1 reduced form in the phi-pass shape the benchmark's `taug1` object
-# was tuned to (four rows per warp, four warps, 64-plane runs; two rows in
-# double-float, where four are refused)
-KERNELS = ["two_pass", "bulk", "auto", "taug1"]
+# autotuner chooses between at 256^3: in their default shapes, and the bulk
+# kernel with 20-plane runs as well, the tuner's pick on some boxes), the
+# library default (the bulk kernel in FP32, the two-pass step in FP64) and
+# the tau_g = 1 reduced form in the phi-pass shape the benchmark's `taug1`
+# object was tuned to (four rows per warp, four warps, 64-plane runs; two
+# rows in double-float, where four are refused)
+KERNELS = ["two_pass", "bulk", "bulk_z20", "auto", "taug1"]
 
 
 def _bench_lattice(params, precision, kernel="auto"):
     from paper_1405_6162_gb300 import Lattice
-    if kernel == "bulk" and precision == "fp64_df":
+    if kernel.startswith("bulk") and precision == "fp64_df":
         pytest.skip("the bulk kernel takes FP64 and FP32-shifted storage")
     if kernel == "taug1" and params["tau_g"] != 1.0:
         pytest.skip("the reduced form needs tau_g = 1")
     shape = ((2 if precision == "fp64_df" else 4), 4, 64) if kernel == "taug1" else ()
+    if kernel == "bulk_z20":
+        kernel, shape = "bulk", (3, 2, 20)
     lat = Lattice.from_params(FULL, params, precision=precision)
     lat.set_kernel(kernel, *shape)
     return lat
