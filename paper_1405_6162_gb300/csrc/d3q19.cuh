@@ -71,15 +71,15 @@ __host__ __device__ constexpr double weight(int i) {
     return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
 }
 
+// x / 2 (exact in binary floating point)
+__device__ __forceinline__ float half(float x) { return 0.5f * x; }
+__device__ __forceinline__ double half(double x) { return 0.5 * x; }
+
 // Relaxation and free-energy parameters in the arithmetic type T.  The
 // relaxation constants fold omega = 1/tau into the lattice weights so that
 // the step evaluates f* = (1 - omega) f + omega feq with one multiply-add
 // per direction (likewise g with omega_g); they are computed in double on
 // the host and rounded once.
-// x / 2 (exact in binary floating point)
-__device__ __forceinline__ float half(float x) { return 0.5f * x; }
-__device__ __forceinline__ double half(double x) { return 0.5 * x; }
-
 template <typename T>
 struct Coll {
     T omega, omega_g;      // 1/tau, 1/tau_g
