@@ -10,8 +10,10 @@ def test_candidates_cover_each_family_and_respect_its_limits():
     assert fams == {"two_pass", "bulk", "fused"}
     # two-pass: threads per CTA x phi sites per thread (the paper's TPB and VVL)
     assert {(c[1], c[2]) for c in c32 if c[0] == "two_pass"} == {(t, v) for t in (128, 256) for v in (1, 2, 4)}
-    # bulk: the lean form (2 slots) only in FP32; cluster sizes divide ny
+    # bulk: the lean form (2 slots) only in FP32; cluster sizes divide ny;
+    # planes per CTA include 20 and 24 (fuller last waves at 256^3)
     assert {c[1] for c in c32 if c[0] == "bulk"} == {2, 3, 4}
+    assert {c[3] for c in c32 if c[0] == "bulk"} == {16, 20, 24, 32, 64}
     c64 = tuning.candidates("fp64", dims, ("bulk",))
     assert {c[1] for c in c64} == {3, 4}
     odd = tuning.candidates("fp32_shifted", (256, 6, 8), ("bulk",))
